@@ -1,0 +1,191 @@
+/*
+ * kr.h -- C interface of the GB300 simultaneous short-recurrence Krylov solvers.
+ *
+ * Solves A X = B for a sparse non-Hermitian A in C^{n x n} and s right-hand sides
+ * B in C^{n x s} with the simultaneous methods of Rashedi, Birk, Frommer, Ebadi,
+ * "On short recurrence Krylov type methods for linear systems with many
+ * right-hand sides" (Sec. 1 states the problem; Secs. 2 and 4 the methods).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Complex numbers are (re, im) pairs of doubles.  An n x s block is n*s
+ * consecutive pairs, row i holding the s entries of unknown i (row-interleaved:
+ * the storage of a C-contiguous (n, s) complex128 array).  An n-vector is n
+ * consecutive pairs.  Device pointers must be 16-byte aligned.
+ *
+ * Every function returns a kr_status; 0 is success.  On any non-zero return a
+ * human-readable message is available from kr_last_error() (thread-local).
+ * Nothing is thrown across the interface and no call traps or aborts.
+ *
+ * `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ * enqueued on it; kr_solve and kr_adjoint_solve additionally synchronise with it
+ * to read the convergence state.  The library is not re-entrant for one kr_op:
+ * do not run two calls on the same operator concurrently.
+ *
+ * Ownership: the library owns an operator's device copies of A and A^H and the
+ * solver workspace cached inside the operator (allocated at the first solve for
+ * a given s and precision, freed by kr_op_destroy).  The caller owns every
+ * B, X, G, Lambda, V, Y and output buffer passed in.
+ */
+#ifndef KR_H_
+#define KR_H_
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KR_API __attribute__((visibility("default")))
+#else
+#define KR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KR_OK = 0,          /* converged: ||R_k||_F <= tol * ||R_0||_F (or call succeeded) */
+  KR_BREAKDOWN = 1,   /* a scalar denominator vanished or an s x s matrix was singular (Sec. 2) */
+  KR_DIVERGED = 2,    /* relative residual above 1e8, or above 1 at the end ("div." in Table 2) */
+  KR_NAN = 3,         /* a non-finite value appeared */
+  KR_MAXIT = 4,       /* iteration limit reached */
+  KR_TIMEOUT = 5,     /* wall-clock limit reached */
+  KR_BAD_ARG = 6,     /* invalid argument (size, pointer, method) */
+  KR_OOM = 7,         /* device allocation failed */
+  KR_CUDA_ERROR = 8,  /* a CUDA call failed */
+  KR_UNSUPPORTED = 9  /* combination not supported (e.g. s > 32) */
+} kr_status;
+
+typedef enum {
+  KR_BL_BICG = 0,         /* Bl-BiCG, Algorithm 3 (Sec. 2) */
+  KR_BL_BICG_RQ = 1,      /* Bl-BiCG-rQ, Algorithm 5 (Sec. 4) */
+  KR_GL_BICG = 2,         /* Gl-BiCG, Algorithm 2 (Sec. 2) */
+  KR_EGL_BICG = 3,        /* eGl-BiCG, Algorithm 4 (Sec. 4) */
+  KR_BL_BICGSTAB = 4,     /* Bl-BiCGStab (Sec. 2; El Guennouni-Jbilou-Sadok) */
+  KR_BL_BICGSTAB_RQ = 5,  /* Bl-BiCGStab-rQ (Sec. 4, last remark) */
+  KR_GL_BICGSTAB = 6,     /* Gl-BiCGStab (Sec. 2, global principle) */
+  KR_BL_QMR = 7,          /* Bl-QMR with block products, no look-ahead (Sec. 2) */
+  KR_GL_QMR = 8,          /* Gl-QMR (Sec. 2, global principle) */
+  KR_EGL_QMR = 9,         /* eGl-QMR (Sec. 4) */
+  KR_LI_BICG = 10         /* Li-BiCG, Algorithm 1 (Sec. 2) */
+} kr_method;
+
+typedef enum {
+  KR_FP64 = 0,        /* complex128 everywhere */
+  KR_FP32_REFINE = 1  /* complex64 inner solves inside an FP64 defect-correction loop */
+} kr_precision;
+
+typedef enum {
+  KR_SHADOW_DEFAULT = 0, /* R^_0 = R_0 (block, global, Li), r^_0 = mean of R_0's columns (economic): Sec. 5 */
+  KR_SHADOW_CONJ = 1,    /* R^_0 = conj(R_0) (Sec. 4) */
+  KR_SHADOW_USER = 2     /* kr_options.shadow holds R^_0 (n x s) or r^_0 (n-vector, economic methods) */
+} kr_shadow;
+
+typedef struct kr_op_s* kr_op;
+
+typedef struct {
+  double tol;             /* relative tolerance on ||R||_F / ||R_0||_F (Sec. 5 uses 1e-10) */
+  int32_t maxit;          /* iteration limit (Sec. 5: 500, 1200 for Example 5) */
+  int32_t precision;      /* kr_precision */
+  double inner_tol;       /* KR_FP32_REFINE: relative tolerance of each inner complex64 solve */
+  int32_t max_outer;      /* KR_FP32_REFINE: limit on defect-correction steps (0 = 30) */
+  int32_t shadow_mode;    /* kr_shadow */
+  const double* shadow;   /* KR_SHADOW_USER: device pointer, layout as B (or an n-vector) */
+  int32_t check_every;    /* read the convergence state back every this many iterations (0 = 8) */
+  int32_t host_buffers;   /* 1: B and X are host pointers (copied to and from the device inside the call) */
+  double* history;        /* optional host array of maxit+1 doubles: ||R_k||_F / ||R_0||_F, k = 0..iters */
+  double time_limit_s;    /* optional wall-clock limit (0 = none) -> KR_TIMEOUT */
+} kr_options;
+
+typedef struct {
+  int32_t iters;            /* iterations performed (inner iterations summed for KR_FP32_REFINE) */
+  int32_t matvecs;          /* single-vector matrix products (2s per Bl/Gl BiCG or QMR iteration) */
+  double relres_recursive;  /* last recursively updated ||R||_F / ||R_0||_F (||C||_F for -rQ) */
+  double relres_true;       /* ||B - A X||_F / ||R_0||_F recomputed in FP64 at exit */
+  int32_t status;           /* kr_status of the iteration */
+  int32_t outer_iters;      /* KR_FP32_REFINE: defect-correction steps */
+} kr_info;
+
+/* Fill *opt with defaults: tol 1e-8, maxit 500, FP64, default shadow, check_every 8. */
+KR_API void kr_options_default(kr_options* opt);
+
+/* Build an operator from a CSR matrix (Sec. 1: A sparse, used only through
+ * matrix-block-vector products A V and A^H W).
+ *   n, nnz        : order and number of stored entries;
+ *   rowptr[n+1]   : int64 row offsets (host), rowptr[0] = 0, rowptr[n] = nnz;
+ *   colidx[nnz]   : int32 column indices (host), each in [0, n);
+ *   vals[2*nnz]   : interleaved (re, im) entries (host);
+ *   device        : CUDA device ordinal that will hold the operator.
+ * The library copies the arrays (the caller keeps ownership), builds A^H as an
+ * explicit CSR, and stores real off-diagonal entries in real form when every
+ * off-diagonal entry has a zero imaginary part.  Returns KR_BAD_ARG for
+ * malformed CSR (checked on the host), KR_OOM when device memory runs out. */
+KR_API kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                           const double* vals, int32_t device, kr_op* out);
+
+/* Release the operator, its device arrays and its cached workspace.  NULL is accepted. */
+KR_API kr_status kr_op_destroy(kr_op op);
+
+/* Order, stored entries, and whether the real-off-diagonal storage is in use. */
+KR_API kr_status kr_op_info(kr_op op, int64_t* n, int64_t* nnz, int32_t* real_offdiag);
+
+/* Matrix-block-vector product (Sec. 1; Algorithms 1-5, first line of the loop):
+ * Y = A V (adjoint = 0) or Y = A^H V (adjoint = 1), V and Y device n x s blocks,
+ * 1 <= s <= 32, V and Y must not overlap. */
+KR_API kr_status kr_op_apply(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, void* stream);
+
+/* Reduction kinds of kr_op_apply_reduce and kr_block_reduce. */
+typedef enum {
+  KR_RED_GRAM = 1,   /* s x s  U^H Y  (Algorithm 3: (Ph^H Q), Algorithm 5: (Vh^H W)) */
+  KR_RED_TRACE = 2,  /* 1      tr(U^H Y)  (Algorithm 2) */
+  KR_RED_SUMV = 3,   /* 1      sum(u^H Y), u an n-vector (Algorithm 4) */
+  KR_RED_NORM2 = 4   /* 1      ||Y||_F^2 (U ignored; result in the real part) */
+} kr_reduction;
+
+/* Block product fused with one reduction of its output: Y = op(A) V and
+ * out = reduce(U, Y).  Y may be NULL (product not stored).  U is a device n x s
+ * block (GRAM, TRACE) or n-vector (SUMV).  out is a device array of s*s (GRAM)
+ * or 1 complex entries, row-major.  Summation order is fixed: repeated calls
+ * give bitwise identical results. */
+KR_API kr_status kr_op_apply_reduce(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, const double* U,
+                             int32_t kind, double* out, void* stream);
+
+/* Stand-alone reduction of two device blocks: out = reduce(U, Y) as above. */
+KR_API kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
+                          void* stream);
+
+/* Thin QR of a device n x s block (Sec. 4, Eq. (QR)): Z = Q S, Q^H Q = I, S upper
+ * triangular with real positive diagonal (CholQR2, shifted first pass when the
+ * Gram matrix is not numerically positive definite).  Q (device n x s, may equal
+ * Z) and S (device s x s, row-major) are written.  KR_BREAKDOWN if Z is
+ * numerically rank deficient. */
+KR_API kr_status kr_thin_qr(int64_t n, int32_t s, const double* Z, double* Q, double* S, void* stream);
+
+/* Solve A X = B with `method` (kr_method) for s right-hand sides, 1 <= s <= 32.
+ * B, X: n x s blocks; device pointers unless opt->host_buffers.  X holds the
+ * initial guess X_0 on entry (the paper uses X_0 = 0, Sec. 5) and the final
+ * iterate on return.  opt may be NULL (defaults).  info may be NULL.
+ * The return value is the iteration status (KR_OK when converged) or an error. */
+KR_API kr_status kr_solve(kr_op op, int32_t method, int32_t s, const double* B, double* X, const kr_options* opt,
+                   void* stream, kr_info* info);
+
+/* Solve the adjoint system A^H Lambda = G with the same simultaneous methods
+ * (roles of A and A^H exchanged); arguments as kr_solve.  Used by reverse-mode
+ * differentiation: for L(X) with X = A^{-1} B, dL/dB = Lambda where
+ * A^H Lambda = dL/dX. */
+KR_API kr_status kr_adjoint_solve(kr_op op, int32_t method, int32_t s, const double* G, double* Lambda,
+                           const kr_options* opt, void* stream, kr_info* info);
+
+/* Gradient with respect to the stored entries of A for X = A^{-1} B and
+ * Lambda = A^{-H} dL/dX:  dL/dA_ij = - sum_c Lambda_ic conj(X_jc) for every stored
+ * (i, j), written as nnz complex values in the order of the CSR given to
+ * kr_op_create_csr (device pointers, dvals of 2*nnz doubles). */
+KR_API kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double* X, double* dvals, void* stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+KR_API const char* kr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KR_H_ */

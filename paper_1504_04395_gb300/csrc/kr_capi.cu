@@ -1,0 +1,456 @@
+// extern "C" boundary of the library (declared in include/kr.h).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/kr.h"
+#include "kr_engine.h"
+#include "kr_solver.h"
+
+struct kr_op_s {
+  kr::Operator op;
+};
+
+namespace kr {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+const char* get_error() { return g_err.c_str(); }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  static std::map<int, int> cache;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  cache[dev] = n;
+  return n;
+}
+
+namespace {
+
+// elementwise helpers of the defect-correction loop and the gradient
+__global__ void to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, int64_t cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void add_c64_kernel(double2* __restrict__ x, const float2* __restrict__ d, int64_t cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = d[i];
+    x[i].x += (double)v.x;
+    x[i].y += (double)v.y;
+  }
+}
+
+// dvals[k] = - sum_c Lambda[i][c] conj(X[j][c]) for stored entry k = (i, j); G threads per row
+template <int G>
+__global__ void __launch_bounds__(256) grad_kernel(int64_t n, int s, const int64_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ colidx,
+                                                   const double2* __restrict__ Lam, const double2* __restrict__ X,
+                                                   double2* __restrict__ dv) {
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane & (G - 1);
+  const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
+  for (int64_t base = blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
+    const int64_t i = base + warp * RPW + lane / G;
+    const bool rowok = i < n;
+    const bool act = rowok && c < s;
+    const double2 l = act ? Lam[i * s + c] : make_double2(0.0, 0.0);
+    int64_t k0 = 0, k1 = 0;
+    if (rowok) { k0 = rowptr[i]; k1 = rowptr[i + 1]; }
+    // iterate to the longest row in the warp so that every lane joins the shuffles
+    int64_t len = k1 - k0, mx = len;
+    for (int off = 16; off >= 1; off >>= 1) {
+      const int64_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+      mx = o > mx ? o : mx;
+    }
+    for (int64_t q = 0; q < mx; ++q) {
+      double2 p = make_double2(0.0, 0.0);
+      const bool has = q < len;
+      if (act && has) {
+        const int64_t j = colidx[k0 + q];
+        const double2 x = X[j * s + c];
+        p.x = l.x * x.x + l.y * x.y;   // l * conj(x)
+        p.y = l.y * x.x - l.x * x.y;
+      }
+      for (int off = G / 2; off >= 1; off >>= 1) {
+        p.x += __shfl_down_sync(0xffffffffu, p.x, off, G);
+        p.y += __shfl_down_sync(0xffffffffu, p.y, off, G);
+      }
+      if (c == 0 && rowok && has) dv[k0 + q] = make_double2(-p.x, -p.y);
+    }
+  }
+}
+
+int grid1d(int64_t cnt) {
+  int64_t g = (cnt + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+kr_status map_exc(const std::exception* e) {
+  if (e) set_error(e->what());
+  return KR_CUDA_ERROR;
+}
+
+#define KR_API_BEGIN try {
+#define KR_API_END                                                                         \
+  }                                                                                        \
+  catch (const ::kr::CudaError& e) {                                                       \
+    ::kr::set_error(std::string(cudaGetErrorString(e.code)) + " (" + e.where + ")");       \
+    return (e.code == cudaErrorMemoryAllocation) ? KR_OOM : KR_CUDA_ERROR;                  \
+  }                                                                                        \
+  catch (const std::bad_alloc&) {                                                          \
+    ::kr::set_error("host allocation failed");                                             \
+    return KR_OOM;                                                                         \
+  }                                                                                        \
+  catch (const std::exception& e) {                                                        \
+    return map_exc(&e);                                                                    \
+  }
+
+// scratch context for the kernel-level entry points (one per device, grown on demand)
+struct Scratch {
+  Operator op;  // empty operator: only n / device are used
+};
+std::map<int, std::unique_ptr<Scratch>> g_scratch;
+std::mutex g_scratch_mu;
+
+Workspace& scratch_ws(int64_t n, int s) {
+  int dev = 0;
+  KR_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  auto& sc = g_scratch[dev];
+  if (!sc) sc = std::make_unique<Scratch>();
+  sc->op.device = dev;
+  if (sc->op.n < n) {  // workspace blocks are sized by n: rebuild when n grows
+    sc->op.ws.clear();
+    sc->op.n = n;
+  }
+  return get_workspace(sc->op, s, sizeof(double2), 0, 0, 1);
+}
+
+bool bad_s(int s) { return s < 1 || s > kMaxS; }
+
+}  // namespace
+}  // namespace kr
+
+using namespace kr;
+
+extern "C" {
+
+void kr_options_default(kr_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->tol = 1e-8;
+  opt->maxit = 500;
+  opt->precision = KR_FP64;
+  opt->inner_tol = 1e-4;
+  opt->max_outer = 30;
+  opt->shadow_mode = KR_SHADOW_DEFAULT;
+  opt->check_every = 8;
+}
+
+const char* kr_last_error(void) { return get_error(); }
+
+kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                           const double* vals, int32_t device, kr_op* out) {
+  if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }
+  *out = nullptr;
+  if (n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && (!colidx || !vals))) {
+    set_error("invalid CSR sizes or NULL arrays");
+    return KR_BAD_ARG;
+  }
+  if (n > 0x7fffffffLL) { set_error("n exceeds int32 column index range"); return KR_BAD_ARG; }
+  if (rowptr[0] != 0 || rowptr[n] != nnz) { set_error("rowptr[0] must be 0 and rowptr[n] == nnz"); return KR_BAD_ARG; }
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) { set_error("rowptr not monotone"); return KR_BAD_ARG; }
+  for (int64_t k = 0; k < nnz; ++k)
+    if (colidx[k] < 0 || colidx[k] >= n) { set_error("column index out of range"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { set_error("no CUDA device"); return KR_CUDA_ERROR; }
+  if (device < 0 || device >= ndev) { set_error("device ordinal out of range"); return KR_BAD_ARG; }
+  KR_CUDA(cudaSetDevice(device));
+  auto h = std::make_unique<kr_op_s>();
+  Operator& op = h->op;
+  op.device = device;
+  op.n = n;
+  op.nnz = nnz;
+  op.h_rowptr.assign(rowptr, rowptr + n + 1);
+  op.h_colidx.assign(colidx, colidx + nnz);
+  op.h_vals.assign(vals, vals + 2 * nnz);
+  build_operator_device(op, false);
+  KR_CUDA(cudaMallocHost(&op.pinned, 4096));
+  *out = h.release();
+  return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_op_destroy(kr_op op) {
+  if (!op) return KR_OK;
+  KR_API_BEGIN
+  delete op;
+  return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_op_info(kr_op op, int64_t* n, int64_t* nnz, int32_t* real_offdiag) {
+  if (!op) { set_error("op is NULL"); return KR_BAD_ARG; }
+  if (n) *n = op->op.n;
+  if (nnz) *nnz = op->op.nnz;
+  if (real_offdiag) *real_offdiag = op->op.real_offdiag;
+  return KR_OK;
+}
+
+static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, const double* U,
+                            int32_t kind, double* out, void* stream) {
+  if (!op || !V || bad_s(s)) { set_error("invalid op, V or s"); return KR_BAD_ARG; }
+  if (kind && (!out || (kind != KR_RED_NORM2 && !U))) { set_error("reduction needs U and out"); return KR_BAD_ARG; }
+  if (kind < 0 || kind > KR_RED_NORM2) { set_error("unknown reduction kind"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace& ws = get_workspace(o, s, sizeof(double2), 0, 0, 1);
+  DevState h{};
+  KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  const CsrDev<double>& M = op_mat<double>(o, adjoint != 0);
+  SpmmArgs<double> a{};
+  a.n = o.n; a.s = s; a.split = M.split; a.rowptr = M.rowptr; a.colidx = M.colidx; a.vals = M.vals;
+  a.offr = M.offr; a.diag = M.diag;
+  a.V = reinterpret_cast<const double2*>(V);
+  a.Y = reinterpret_cast<double2*>(Y);
+  a.ay = 1.0;
+  RedSet rs{};
+  rs.partials = ws.partials;
+  if (kind) {
+    rs.nred = 1;
+    rs.r[0].kind = kind;
+    rs.r[0].ureg = -1;
+    rs.r[0].U = U;
+    rs.nslots = kind == KR_RED_GRAM ? s * s : 1;
+  }
+  const int grid = row_grid(o.n, s);
+  launch_spmm<double>(a, rs, grid, nullptr, st);
+  if (kind) launch_reduce<double>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
+  return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_op_apply(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, void* stream) {
+  if (!Y) { set_error("Y is NULL"); return KR_BAD_ARG; }
+  return apply_impl(op, adjoint, s, V, Y, nullptr, 0, nullptr, stream);
+}
+
+kr_status kr_op_apply_reduce(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, const double* U,
+                             int32_t kind, double* out, void* stream) {
+  if (kind < KR_RED_GRAM || kind > KR_RED_NORM2) { set_error("unknown reduction kind"); return KR_BAD_ARG; }
+  return apply_impl(op, adjoint, s, V, Y, U, kind, out, stream);
+}
+
+kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
+                          void* stream) {
+  if (n <= 0 || bad_s(s) || !Y || !out || (kind != KR_RED_NORM2 && !U) || kind < KR_RED_GRAM || kind > KR_RED_NORM2) {
+    set_error("invalid arguments");
+    return KR_BAD_ARG;
+  }
+  KR_API_BEGIN
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace& ws = scratch_ws(n, s);
+  LinArgs a{};
+  a.n = n;
+  a.s = s;
+  a.nout = 1;
+  a.o[0].nterm = 1;
+  a.o[0].t[0].src_kind = SRC_BLOCK;
+  a.o[0].t[0].src = Y;
+  a.o[0].t[0].coef_kind = COEF_ONE;
+  RedSet rs{};
+  rs.partials = ws.partials;
+  rs.nred = 1;
+  rs.r[0].kind = kind;
+  rs.r[0].ysrc = 0;
+  rs.r[0].ureg = -1;
+  rs.r[0].U = U;
+  rs.nslots = kind == KR_RED_GRAM ? s * s : 1;
+  const int grid = row_grid(n, s);
+  const int G = threads_per_row(s);
+  if (kind == KR_RED_GRAM && ng_capacity(G) < 1) { set_error("Gram with s > 16 not fused here"); return KR_UNSUPPORTED; }
+  launch_lincomb<double>(a, rs, grid, nullptr, st);
+  launch_reduce<double>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
+  return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_thin_qr(int64_t n, int32_t s, const double* Z, double* Q, double* S, void* stream) {
+  if (n <= 0 || bad_s(s) || !Z || !Q || !S) { set_error("invalid arguments"); return KR_BAD_ARG; }
+  if (s > 16) { set_error("kr_thin_qr supports s <= 16"); return KR_UNSUPPORTED; }
+  KR_API_BEGIN
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace& ws = scratch_ws(n, s);
+  if (Q != Z) KR_CUDA(cudaMemcpyAsync(Q, Z, sizeof(double2) * n * s, cudaMemcpyDeviceToDevice, st));
+  DevState h{};
+  h.maxit = 1;
+  KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  int dev = 0;
+  KR_CUDA(cudaGetDevice(&dev));
+  Operator& o = g_scratch[dev]->op;
+  standalone_qr(o, ws, n, s, Q, st);
+  KR_CUDA(cudaMemcpyAsync(S, ws.arena + (size_t)SL_QR_S * kSlotElems, sizeof(double2) * s * s,
+                          cudaMemcpyDeviceToDevice, st));
+  DevState back{};
+  KR_CUDA(cudaMemcpyAsync(&back, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  KR_CUDA(cudaStreamSynchronize(st));
+  if (back.done && back.status == 1) { set_error("rank-deficient block"); return KR_BREAKDOWN; }
+  return KR_OK;
+  KR_API_END
+}
+
+static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B, double* X, const kr_options* optp,
+                            void* stream, kr_info* info, bool adjoint) {
+  if (!op || !B || !X) { set_error("op, B and X must be non-NULL"); return KR_BAD_ARG; }
+  if (method < 0 || method >= KRM_COUNT) { set_error("unknown method"); return KR_BAD_ARG; }
+  if (bad_s(s)) { set_error("s must be in [1, 32]"); return KR_UNSUPPORTED; }
+  kr_options opt;
+  if (optp) opt = *optp; else kr_options_default(&opt);
+  if (!(opt.tol >= 0.0) || opt.maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return KR_BAD_ARG; }
+  if (opt.shadow_mode == KR_SHADOW_USER && !opt.shadow) { set_error("user shadow is NULL"); return KR_BAD_ARG; }
+  if (opt.precision != KR_FP64 && opt.precision != KR_FP32_REFINE) { set_error("unknown precision"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(double2) * (size_t)o.n * s;
+  const double* dB = B;
+  double* dX = X;
+  void *tB = nullptr, *tX = nullptr;
+  struct Guard {
+    void** a; void** b;
+    ~Guard() { if (*a) cudaFree(*a); if (*b) cudaFree(*b); }
+  } guard{&tB, &tX};
+  if (opt.host_buffers) {
+    KR_CUDA(cudaMalloc(&tB, bytes));
+    KR_CUDA(cudaMalloc(&tX, bytes));
+    KR_CUDA(cudaMemcpyAsync(tB, B, bytes, cudaMemcpyHostToDevice, st));
+    KR_CUDA(cudaMemcpyAsync(tX, X, bytes, cudaMemcpyHostToDevice, st));
+    dB = reinterpret_cast<const double*>(tB);
+    dX = reinterpret_cast<double*>(tX);
+  }
+  SolveIn in;
+  in.tol = opt.tol;
+  in.maxit = opt.maxit;
+  in.check_every = opt.check_every > 0 ? opt.check_every : 8;
+  in.shadow_mode = opt.shadow_mode;
+  in.shadow = opt.shadow;
+  in.time_limit_s = opt.time_limit_s;
+  kr_info inf{};
+  if (opt.precision == KR_FP64) {
+    SolveOut so = run_solve<double>(o, method, s, dB, dX, in, st, adjoint);
+    inf.iters = so.iters;
+    inf.matvecs = so.matvecs;
+    inf.status = so.status;
+    inf.relres_recursive = so.relres_recursive;
+    const double tr = true_residual(o, s, dB, dX, nullptr, st, adjoint);
+    inf.relres_true = so.res0 > 0 ? tr / so.res0 : tr;
+    if (opt.history)
+      for (size_t k = 0; k < so.hist.size() && (int)k <= opt.maxit; ++k) opt.history[k] = so.hist[k];
+  } else {
+    // defect correction: R = B - A X in FP64; inner complex64 solve of A D = R; X += D
+    build_operator_device(o, true);
+    Workspace& rw = get_workspace(o, s, 24, 3, 0, 1);  // R64, R32, D32 (sized for complex128)
+    void *R64 = rw.blocks[0], *R32 = rw.blocks[1], *D32 = rw.blocks[2];
+    const int64_t cnt = o.n * (int64_t)s;
+    double res0 = true_residual(o, s, dB, dX, R64, st, adjoint);
+    double res = res0;
+    SolveIn inner = in;
+    inner.tol = opt.inner_tol > 0 ? opt.inner_tol : 1e-4;
+    inner.shadow_mode = opt.shadow_mode == KR_SHADOW_USER ? KR_SHADOW_DEFAULT : opt.shadow_mode;
+    const int max_outer = opt.max_outer > 0 ? opt.max_outer : 30;
+    int status = KR_MAXIT, outer = 0;
+    if (opt.history) opt.history[0] = 1.0;
+    if (res0 == 0.0) status = KR_OK;
+    else if (!std::isfinite(res0)) status = KR_NAN;
+    while (status == KR_MAXIT && outer < max_outer && inf.iters < opt.maxit) {
+      inner.maxit = opt.maxit - inf.iters;
+      to_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<const double2*>(R64),
+                                                  reinterpret_cast<float2*>(R32), cnt);
+      KR_CUDA(cudaGetLastError());
+      KR_CUDA(cudaMemsetAsync(D32, 0, sizeof(float2) * cnt, st));
+      SolveOut so = run_solve<float>(o, method, s, R32, D32, inner, st, adjoint);
+      inf.iters += so.iters;
+      inf.matvecs += so.matvecs;
+      add_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<double2*>(dX),
+                                                   reinterpret_cast<const float2*>(D32), cnt);
+      KR_CUDA(cudaGetLastError());
+      const double prev = res;
+      res = true_residual(o, s, dB, dX, R64, st, adjoint);
+      ++outer;
+      if (opt.history && outer <= opt.maxit) opt.history[outer] = res / res0;
+      if (!std::isfinite(res)) status = KR_NAN;
+      else if (res <= opt.tol * res0) status = KR_OK;
+      else if (res >= prev && (so.status == KR_BREAKDOWN || so.status == KR_NAN || so.iters == 0))
+        status = so.status == KR_NAN ? KR_NAN : KR_BREAKDOWN;
+      else if (res > 1e8 * res0) status = KR_DIVERGED;
+    }
+    inf.outer_iters = outer;
+    inf.status = status;
+    inf.relres_recursive = res0 > 0 ? res / res0 : res;
+    inf.relres_true = inf.relres_recursive;
+  }
+  if (inf.status == KR_MAXIT && inf.relres_true > 1.0) inf.status = KR_DIVERGED;
+  if (!std::isfinite(inf.relres_true) && inf.status != KR_BREAKDOWN) inf.status = KR_NAN;
+  if (opt.host_buffers) {
+    KR_CUDA(cudaMemcpyAsync(X, tX, bytes, cudaMemcpyDeviceToHost, st));
+    KR_CUDA(cudaStreamSynchronize(st));
+  }
+  if (info) *info = inf;
+  return static_cast<kr_status>(inf.status);
+  KR_API_END
+}
+
+kr_status kr_solve(kr_op op, int32_t method, int32_t s, const double* B, double* X, const kr_options* opt,
+                   void* stream, kr_info* info) {
+  return solve_impl(op, method, s, B, X, opt, stream, info, false);
+}
+
+kr_status kr_adjoint_solve(kr_op op, int32_t method, int32_t s, const double* G, double* Lambda,
+                           const kr_options* opt, void* stream, kr_info* info) {
+  return solve_impl(op, method, s, G, Lambda, opt, stream, info, true);
+}
+
+kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double* X, double* dvals, void* stream) {
+  if (!op || !Lambda || !X || !dvals || bad_s(s)) { set_error("invalid arguments"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ensure_orig_pattern(o);
+  const int G = threads_per_row(s);
+  const int grid = row_grid(o.n, s);
+  const auto* L = reinterpret_cast<const double2*>(Lambda);
+  const auto* Xp = reinterpret_cast<const double2*>(X);
+  auto* dv = reinterpret_cast<double2*>(dvals);
+  switch (G) {
+    case 1: grad_kernel<1><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+    case 2: grad_kernel<2><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+    case 4: grad_kernel<4><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+    case 8: grad_kernel<8><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+    case 16: grad_kernel<16><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+    default: grad_kernel<32><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
+  }
+  KR_CUDA(cudaGetLastError());
+  return KR_OK;
+  KR_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Row kernels over n x s blocks: block sparse product (SpMM), row-local linear
+// combinations, and the fused reductions (Gram, trace, sum, norm) they feed.
+//
+// Thread mapping: G threads per row (G a power of two >= s), thread c of a row
+// group owning column c; 32/G rows per warp; 256 threads per CTA; a grid-stride
+// loop over rows with a grid size fixed by n, so every CTA's partial sums, and
+// hence every reduction, are formed in a fixed order (bitwise reproducible).
+#pragma once
+
+#include "kr_common.cuh"
+
+namespace kr {
+
+constexpr int kMaxRed = 4;     // fused reductions per launch
+constexpr int kMaxOut = 6;     // outputs of one linear-combination launch
+constexpr int kMaxTerm = 4;    // terms per output
+constexpr int kMaxMat = 6;     // s x s / diagonal coefficient matrices per launch
+
+struct RedSpec {
+  int kind;        // RedKind
+  int ysrc;        // which computed value is Y (linear combination: output index; SpMM: 0)
+  int ureg;        // >= 0: U is computed output ureg of this launch; -1: U is read from memory
+  int gacc;        // accumulator index for RED_GRAM
+  const void* U;   // memory operand: n x s block (GRAM, TRACE) or n-vector (SUMV, GRAMV)
+  int slot;        // first slot of this reduction in a CTA's partial record
+  int pad;
+};
+
+struct RedSet {
+  int nred;
+  int nslots;      // slots per CTA record
+  void* partials;  // [gridDim.x][nslots] complex (C2<T>)
+  RedSpec r[kMaxRed];
+};
+
+// ---------------------------------------------------------------------------------------
+// SpMM: Y = ay * (A V) + bz * Z  (ay, bz real; optionally ay scaled by a device scalar)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct SpmmArgs {
+  int64_t n;
+  int s;
+  int split;                 // 1: real off-diagonal entries + complex diagonal
+  const int64_t* rowptr;
+  const int32_t* colidx;
+  const C2<T>* vals;         // complex entries (split == 0)
+  const T* offr;             // real off-diagonal entries (split == 1)
+  const C2<T>* diag;         // complex diagonal (split == 1)
+  const C2<T>* V;            // input block, row stride s
+  C2<T>* Y;                  // output block (may be null: reductions only)
+  const C2<T>* Z;            // optional addend block
+  double ay, bz;             // real scales
+  const double2* ys;         // optional device scalar multiplying ay (complex)
+  int ys_conj, ys_neg;
+};
+
+// ---------------------------------------------------------------------------------------
+// Linear combinations: out_o = sum_t  src_t * coef_t
+// ---------------------------------------------------------------------------------------
+enum SrcKind : int { SRC_BLOCK = 0, SRC_VEC = 1, SRC_REG = 2 };
+enum CoefKind : int { COEF_ONE = 0, COEF_SCALAR = 1, COEF_MAT = 2, COEF_DIAG = 3, COEF_REAL = 4 };
+
+struct Term {
+  int src_kind;        // SrcKind
+  int src_reg;         // SRC_REG: index of an earlier output
+  const void* src;     // SRC_BLOCK / SRC_VEC pointer
+  int coef_kind;       // CoefKind
+  int coef_idx;        // COEF_MAT / COEF_DIAG: index into the launch's matrix table
+  const double2* coef; // COEF_SCALAR: device complex scalar
+  double creal;        // COEF_REAL: host real scalar
+  int neg, conj;       // flags on the coefficient (negate; conjugate scalar / diagonal)
+  int xconj;           // conjugate the source value
+};
+
+struct Out {
+  int nterm;
+  int is_vec;          // output is an n-vector (stored by column-0 threads)
+  void* dst;           // null: temporary (kept only for reductions / later terms)
+  Term t[kMaxTerm];
+};
+
+struct LinArgs {
+  int64_t n;
+  int s;
+  int nout;
+  int nmat;
+  const double2* mat[kMaxMat];   // device s x s (row-major) or s-vector (diagonal) coefficients
+  int mat_is_diag[kMaxMat];
+  Out o[kMaxOut];
+};
+
+}  // namespace kr

