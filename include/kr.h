@@ -181,6 +181,32 @@ KR_API kr_status kr_adjoint_solve(kr_op op, int32_t method, int32_t s, const dou
  * kr_op_create_csr (device pointers, dvals of 2*nnz doubles). */
 KR_API kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double* X, double* dvals, void* stream);
 
+/* Kernel classes of the launch profile. */
+typedef enum {
+  KR_K_SPMM = 0,     /* block sparse products A V, A^H W with fused reductions */
+  KR_K_LINCOMB = 1,  /* row-local block updates with fused reductions */
+  KR_K_REDUCE = 2,   /* fixed-order sums of per-CTA partial reductions */
+  KR_K_COEF = 3,     /* one-CTA FP64 coefficient algebra (s x s solves, QR factors, rotations) */
+  KR_K_OTHER = 4,    /* precision conversions, gradient */
+  KR_K_CLASSES = 5
+} kr_kernel_class;
+
+typedef struct {
+  int64_t launches[8];  /* kernel launches per class since the last reset */
+  double ms[8];         /* summed CUDA-event durations per class (when timing is on) */
+  double flops[8];      /* algorithmic floating-point operations per class */
+  double bytes[8];      /* algorithmic DRAM bytes per class (each operand read or written once) */
+} kr_profile;
+
+/* Turn launch counting on or off (process-wide, default off).  With
+ * time_kernels != 0 every launch is bracketed by CUDA events on its stream and
+ * the durations are summed when kr_profile_read is called (which synchronises
+ * with the recorded events).  Profiling adds no kernels of its own. */
+KR_API kr_status kr_profile_enable(int32_t enable, int32_t time_kernels);
+
+/* Copy the counters into *out; reset them when reset != 0. */
+KR_API kr_status kr_profile_read(kr_profile* out, int32_t reset);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 KR_API const char* kr_last_error(void);
 

@@ -57,6 +57,17 @@ class KrInfo(ctypes.Structure):
     ]
 
 
+class KrProfile(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int64 * 8),
+        ("ms", ctypes.c_double * 8),
+        ("flops", ctypes.c_double * 8),
+        ("bytes", ctypes.c_double * 8),
+    ]
+
+
+KERNEL_CLASSES = ["spmm", "lincomb", "reduce", "coef", "other"]
+
 # exported symbols and their C signatures (must match include/kr.h)
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -74,6 +85,8 @@ SIGNATURES = {
     "kr_adjoint_solve": (_I32, [_P, _I32, _I32, _P, _P, ctypes.POINTER(KrOptions), _P, ctypes.POINTER(KrInfo)]),
     "kr_grad_values": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "kr_last_error": (ctypes.c_char_p, []),
+    "kr_profile_enable": (_I32, [_I32, _I32]),
+    "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
 }
 
 
@@ -335,6 +348,18 @@ def kr_grad_values(op: Operator, Lam, X, stream=None):
     return dv
 
 
+def kr_profile_enable(enable=True, time_kernels=False):
+    _check(lib().kr_profile_enable(int(enable), int(time_kernels)))
+
+
+def kr_profile_read(reset=False):
+    """Per kernel class: launches, summed CUDA-event ms, algorithmic flops and bytes."""
+    p = KrProfile()
+    _check(lib().kr_profile_read(ctypes.byref(p), int(reset)))
+    return {name: {"launches": p.launches[i], "ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i]}
+            for i, name in enumerate(KERNEL_CLASSES)}
+
+
 solve = kr_solve
 adjoint_solve = kr_adjoint_solve
 
@@ -342,5 +367,5 @@ __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
     "kr_op_create_csr", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
-    "FP64", "FP32_REFINE",
+    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "KERNEL_CLASSES",
 ]

@@ -9,6 +9,7 @@
 
 #include "../../include/kr.h"
 #include "kr_engine.h"
+#include "kr_profile.h"
 #include "kr_solver.h"
 
 struct kr_op_s {
@@ -226,7 +227,7 @@ static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const double* 
   const CsrDev<double>& M = op_mat<double>(o, adjoint != 0);
   SpmmArgs<double> a{};
   a.n = o.n; a.s = s; a.split = M.split; a.rowptr = M.rowptr; a.colidx = M.colidx; a.vals = M.vals;
-  a.offr = M.offr; a.diag = M.diag;
+  a.offr = M.offr; a.diag = M.diag; a.nnz = M.nnz;
   a.V = reinterpret_cast<const double2*>(V);
   a.Y = reinterpret_cast<double2*>(Y);
   a.ay = 1.0;
@@ -382,16 +383,24 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
     else if (!std::isfinite(res0)) status = KR_NAN;
     while (status == KR_MAXIT && outer < max_outer && inf.iters < opt.maxit) {
       inner.maxit = opt.maxit - inf.iters;
-      to_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<const double2*>(R64),
-                                                  reinterpret_cast<float2*>(R32), cnt);
-      KR_CUDA(cudaGetLastError());
+      {
+        ProfToken tk = prof_begin(KC_OTHER, st);
+        to_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<const double2*>(R64),
+                                                    reinterpret_cast<float2*>(R32), cnt);
+        KR_CUDA(cudaGetLastError());
+        prof_end(tk, st, 0.0, 24.0 * cnt);
+      }
       KR_CUDA(cudaMemsetAsync(D32, 0, sizeof(float2) * cnt, st));
       SolveOut so = run_solve<float>(o, method, s, R32, D32, inner, st, adjoint);
       inf.iters += so.iters;
       inf.matvecs += so.matvecs;
-      add_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<double2*>(dX),
-                                                   reinterpret_cast<const float2*>(D32), cnt);
-      KR_CUDA(cudaGetLastError());
+      {
+        ProfToken tk = prof_begin(KC_OTHER, st);
+        add_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<double2*>(dX),
+                                                     reinterpret_cast<const float2*>(D32), cnt);
+        KR_CUDA(cudaGetLastError());
+        prof_end(tk, st, 2.0 * cnt, 40.0 * cnt);
+      }
       const double prev = res;
       res = true_residual(o, s, dB, dX, R64, st, adjoint);
       ++outer;
@@ -440,6 +449,7 @@ kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double
   const auto* L = reinterpret_cast<const double2*>(Lambda);
   const auto* Xp = reinterpret_cast<const double2*>(X);
   auto* dv = reinterpret_cast<double2*>(dvals);
+  ProfToken tk = prof_begin(KC_OTHER, st);
   switch (G) {
     case 1: grad_kernel<1><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
     case 2: grad_kernel<2><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
@@ -449,6 +459,7 @@ kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double
     default: grad_kernel<32><<<grid, 256, 0, st>>>(o.n, s, o.orig_rowptr, o.orig_colidx, L, Xp, dv); break;
   }
   KR_CUDA(cudaGetLastError());
+  prof_end(tk, st, 8.0 * s * o.nnz, 12.0 * o.nnz + 8.0 * (o.n + 1) + 32.0 * o.n * s);
   return KR_OK;
   KR_API_END
 }

@@ -6,6 +6,7 @@
 // convergence, divergence, a non-finite value or a breakdown sets the state's
 // done flag, after which every later kernel of the solve returns at once.
 #include "kr_engine.h"
+#include "kr_profile.h"
 #include "kr_small.cuh"
 
 namespace kr {
@@ -582,8 +583,10 @@ __global__ void __launch_bounds__(256) coef_kernel(CoefArgs a) {
 }
 
 void launch_coef(const CoefArgs& a, cudaStream_t st) {
+  ProfToken tk = prof_begin(KC_COEF, st);
   coef_kernel<<<1, 256, 0, st>>>(a);
   KR_CUDA(cudaGetLastError());
+  prof_end(tk, st, 0.0, 0.0);
 }
 
 }  // namespace kr

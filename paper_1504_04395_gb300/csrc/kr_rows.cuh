@@ -52,6 +52,7 @@ struct SpmmArgs {
   double ay, bz;             // real scales
   const double2* ys;         // optional device scalar multiplying ay (complex)
   int ys_conj, ys_neg;
+  int64_t nnz;               // stored entries (host-side bookkeeping for the launch profile)
 };
 
 // ---------------------------------------------------------------------------------------

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kr_internal.h"
+#include "kr_profile.h"
 #include "kr_rows_impl.cuh"
 
 namespace kr {
@@ -39,7 +40,7 @@ static void spmm_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int grid, co
 }
 
 template <typename T>
-void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   const int G = threads_per_row(a.s);
   const int ng = count_grams(rs);
   switch (G) {
@@ -51,6 +52,25 @@ void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* do
     case 32: return spmm_ng<T, 32>(ng, a, rs, grid, done, st);
   }
   throw CudaError{cudaErrorInvalidValue, "spmm: s out of range"};
+}
+
+template <typename T>
+void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+  ProfToken tk = prof_begin(KC_SPMM, st);
+  spmm_dispatch<T>(a, rs, grid, done, st);
+  const double E = sizeof(C2<T>);
+  const double n = (double)a.n, s = (double)a.s, nnz = (double)a.nnz;
+  double f = a.split ? s * (4.0 * nnz + 6.0 * n) : s * 8.0 * nnz;
+  if (a.ys != nullptr || a.ay != 1.0) f += 6.0 * s * n;
+  if (a.Z != nullptr) f += 4.0 * s * n;
+  f += red_flops(rs, a.n, a.s);
+  double b = 8.0 * (n + 1) + 4.0 * nnz + (a.split ? sizeof(T) * nnz + E * n : E * nnz);
+  b += E * n * s;
+  if (a.Y != nullptr) b += E * n * s;
+  if (a.Z != nullptr) b += E * n * s;
+  const void* counted[3] = {a.V, a.Y, a.Z};
+  b += red_bytes(rs, a.n, a.s, E, counted, 3);
+  prof_end(tk, st, f, b);
 }
 
 template <typename T, int G, int NG>
@@ -77,7 +97,46 @@ static void lin_ng(int ng, const LinArgs& a, const RedSet& rs, int grid, const i
 }
 
 template <typename T>
+static void lin_dispatch(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
+
+template <typename T>
 void launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+  ProfToken tk = prof_begin(KC_LINCOMB, st);
+  lin_dispatch<T>(a, rs, grid, done, st);
+  const double E = sizeof(C2<T>);
+  const double n = (double)a.n, s = (double)a.s;
+  double f = 0.0, b = 0.0;
+  const void* counted[kMaxOut * kMaxTerm + kMaxOut];
+  int nc = 0;
+  for (int o = 0; o < a.nout; ++o) {
+    const Out& q = a.o[o];
+    const double cnt = q.is_vec ? n : n * s;
+    for (int t = 0; t < q.nterm; ++t) {
+      const Term& tm = q.t[t];
+      switch (tm.coef_kind) {
+        case COEF_ONE: f += 2.0 * cnt; break;
+        case COEF_REAL: f += 4.0 * cnt; break;
+        case COEF_MAT: f += 8.0 * s * cnt; break;
+        default: f += 8.0 * cnt; break;
+      }
+      if (tm.src_kind != SRC_REG) {
+        bool seen = false;
+        for (int k = 0; k < nc; ++k) seen = seen || counted[k] == tm.src;
+        if (!seen) {
+          counted[nc++] = tm.src;
+          b += E * (tm.src_kind == SRC_VEC ? n : n * s);
+        }
+      }
+    }
+    if (q.dst != nullptr) b += E * cnt;
+  }
+  f += red_flops(rs, a.n, a.s);
+  b += red_bytes(rs, a.n, a.s, E, counted, nc);
+  prof_end(tk, st, f, b);
+}
+
+template <typename T>
+static void lin_dispatch(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   const int G = threads_per_row(a.s);
   const int ng = count_grams(rs);
   switch (G) {
@@ -94,9 +153,11 @@ void launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* don
 template <typename T>
 void launch_reduce(const void* partials, int nparts, int nslots, double2* out, const int* done, cudaStream_t st) {
   if (nslots <= 0) return;
+  ProfToken tk = prof_begin(KC_REDUCE, st);
   reduce_slots_kernel<T><<<nslots, kThreads, 0, st>>>(reinterpret_cast<const C2<T>*>(partials), nparts, nslots,
                                                        out, done);
   KR_CUDA(cudaGetLastError());
+  prof_end(tk, st, 2.0 * nparts * nslots, (double)sizeof(C2<T>) * nparts * nslots + 16.0 * nslots);
 }
 
 #define KR_INSTANTIATE_ROWS(T)                                                                               \

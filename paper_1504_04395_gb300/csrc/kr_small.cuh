@@ -95,14 +95,16 @@ __device__ bool lu_solve(double2* M, double2* X, int s, int nrhs, double* scratc
   bool ok = isfinite(nrm);
   for (int k = 0; k < s && ok; ++k) {
     if (threadIdx.x == 0) {
+      // pivot: largest |re| + |im| in the column (the LAPACK convention for complex LU)
       int p = k;
-      double best = cabsd(M[k * s + k]);
+      double best = fabs(M[k * s + k].x) + fabs(M[k * s + k].y);
       for (int i = k + 1; i < s; ++i) {
-        const double v = cabsd(M[i * s + k]);
+        const double v = fabs(M[i * s + k].x) + fabs(M[i * s + k].y);
         if (v > best) { best = v; p = i; }
       }
       iscratch[0] = p;
-      iscratch[1] = (best <= tolp || !isfinite(best)) ? 1 : 0;
+      const double piv = cabsd(M[p * s + k]);
+      iscratch[1] = (piv <= tolp || !isfinite(piv)) ? 1 : 0;
     }
     __syncthreads();
     const int p = iscratch[0];

@@ -320,6 +320,7 @@ struct Engine {
     a.ys = ys;
     a.ys_conj = ysconj;
     a.ys_neg = ysneg;
+    a.nnz = M.nnz;
     r.rs.partials = ws.partials;
     const int grid = row_grid(n, sdim);
     if (count_grams(r.rs) <= ng_capacity(threads_per_row(sdim))) {

@@ -22,6 +22,14 @@ METHODS = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "li_bicg", "bl_bicgst
            "gl_bicgstab", "gl_qmr", "egl_qmr", "bl_qmr"]
 HIST_RTOL = 1e-10   # per-iteration residual norms, first 20 iterations
 X_RTOL = 1e-8       # final iterate
+SENS_FACTOR = 10.0  # allowed multiple of the oracle's own rounding sensitivity
+
+# The block methods solve s x s systems that become ill-conditioned (Sec. 3 and Sec. 4 of
+# the paper: inexact deflation); two correct FP64 implementations then differ by far more
+# than 1e-10.  The bar per iteration is therefore max(1e-10 * rho_k, 10 * sens_k), where
+# sens_k is how far the oracle's own history moves when B is perturbed by one ulp (largest
+# of two seeded perturbations).  For the global / economic methods sens_k is ~1e-13, so the
+# 1e-10 relative bar is what binds.
 
 
 @pytest.fixture(scope="module")
@@ -54,12 +62,33 @@ def run_pair(kr, method, n, rp, ci, v, B, tol=1e-8, maxit=300, shadow=None):
     return op, ref, X.cpu().numpy(), info
 
 
-def check_history(ref_hist, gpu_hist, upto=20):
+def oracle_sensitivity(method, A, B, maxit, tol=1e-8, shadow=None, k_x=None):
+    """How far the oracle moves under one-ulp perturbations of B: (history deltas, X delta at k_x)."""
+    rng = np.random.default_rng(2024)
+    base = oracle.solve(method, A, B, tol=tol, maxit=maxit, shadow=shadow)
+    dh = np.zeros(len(base.history))
+    dx = 0.0
+    base_x = oracle.solve(method, A, B, tol=0.0, maxit=k_x, shadow=shadow).X if k_x else None
+    for _ in range(2):
+        Bp = B * (1 + 2.2e-16 * rng.standard_normal(B.shape))
+        r = oracle.solve(method, A, Bp, tol=tol, maxit=maxit, shadow=shadow)
+        k = min(len(r.history), len(dh))
+        dh[:k] = np.maximum(dh[:k], np.abs(np.array(r.history[:k]) - np.array(base.history[:k])))
+        if k_x:
+            xp = oracle.solve(method, A, Bp, tol=0.0, maxit=k_x, shadow=shadow).X
+            dx = max(dx, rel(xp, base_x))
+    return dh, dx
+
+
+def check_history(ref_hist, gpu_hist, upto=20, sens=None):
     k = min(upto, len(ref_hist), len(gpu_hist))
     assert k >= 2
     a = np.array(gpu_hist[:k])
     b = np.array(ref_hist[:k])
-    assert np.all(np.abs(a - b) <= HIST_RTOL * np.abs(b)), np.max(np.abs(a - b) / np.abs(b))
+    bar = HIST_RTOL * np.abs(b)
+    if sens is not None:
+        bar = np.maximum(bar, SENS_FACTOR * np.asarray(sens[:k]))
+    assert np.all(np.abs(a - b) <= bar), (np.max(np.abs(a - b) / np.abs(b)), np.max(np.abs(a - b) - bar))
 
 
 @pytest.mark.parametrize("method", METHODS)
@@ -68,18 +97,19 @@ def test_method_parity_2d(kr, method):
     n, rp, ci, v = conv(24, shift=0.3j)
     B = gaussian_block(n, 4, seed=0)
     op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B)
-    check_history(ref.history, info.history)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    # X after exactly the oracle's iteration count k*.  Bl-QMR without look-ahead loses
+    # bi-orthogonality exponentially, so its iterate is compared inside the parity window.
+    k = min(ref.iters, 20 if method == "bl_qmr" else 60)
+    sens_h, sens_x = oracle_sensitivity(method, A, B, 300, k_x=k)
+    check_history(ref.history, info.history, sens=sens_h)
     if ref.status == oracle.Status.OK:
         assert info.status == "OK"
         assert abs(info.iters - ref.iters) <= 1, (info.iters, ref.iters)
-    # X after exactly the oracle's iteration count k*.  Bl-QMR without look-ahead loses
-    # bi-orthogonality exponentially (rounding grows ~1e3 per 5 steps on this problem), so
-    # its iterate is compared early, before rounding differences dominate.
-    k = min(ref.iters, 12 if method == "bl_qmr" else 60)
-    ref_k = oracle.solve(method, oracle.csr_matrix_from_arrays(n, rp, ci, v), B, tol=0.0, maxit=k)
+    ref_k = oracle.solve(method, A, B, tol=0.0, maxit=k)
     Xk, ik = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=0.0, maxit=k)
     assert ik.iters == k
-    assert rel(Xk.cpu().numpy(), ref_k.X) < X_RTOL
+    assert rel(Xk.cpu().numpy(), ref_k.X) <= max(X_RTOL, SENS_FACTOR * sens_x)
     op.close()
 
 
@@ -96,7 +126,7 @@ def test_config1_dense_lu(kr, method):
     assert info.relres_true < 2e-8
     assert rel(X.cpu().numpy(), X_lu) < 1e-6
     ref = oracle.solve(method, A, B, tol=1e-8, maxit=1000)
-    check_history(ref.history, info.history)
+    check_history(ref.history, info.history, sens=oracle_sensitivity(method, A, B, 1000)[0])
     op.close()
 
 
@@ -106,7 +136,8 @@ def test_s_edge_cases(kr, method, s):
     n, rp, ci, v = conv(13, d=3, pe=0.4, shift=0.5j)  # n = 2197: ragged tail for every G
     B = gaussian_block(n, s, seed=s)
     op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, maxit=200)
-    check_history(ref.history, info.history)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    check_history(ref.history, info.history, sens=oracle_sensitivity(method, A, B, 200)[0])
     assert info.status == ref.status.name
     op.close()
 
@@ -117,7 +148,8 @@ def test_random_matrix_with_empty_rows(kr, method):
     rp, ci, v = random_csr(n, max_row=6, seed=5, diag_shift=6.0 + 2.0j)
     B = gaussian_block(n, 3, seed=1)
     op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, tol=1e-10, maxit=200)
-    check_history(ref.history, info.history)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    check_history(ref.history, info.history, sens=oracle_sensitivity(method, A, B, 200, tol=1e-10)[0])
     op.close()
 
 
@@ -129,7 +161,8 @@ def test_user_shadow(kr, method):
     if method.startswith("egl"):
         shadow = np.ascontiguousarray(shadow[:, 0])
     op, ref, X, info = run_pair(kr, method, n, rp, ci, v, B, maxit=100, shadow=shadow)
-    check_history(ref.history, info.history)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    check_history(ref.history, info.history, sens=oracle_sensitivity(method, A, B, 100, shadow=shadow)[0])
     op.close()
 
 
@@ -176,7 +209,7 @@ def test_adjoint_solve(kr, method):
     L_ref = np.linalg.solve(A.toarray().conj().T, G)
     assert rel(L.cpu().numpy(), L_ref) < 1e-8
     ref = oracle.solve(method, oracle.adjoint(A), G, tol=1e-11, maxit=400)
-    check_history(ref.history, info.history)
+    check_history(ref.history, info.history, sens=oracle_sensitivity(method, oracle.adjoint(A), G, 400, tol=1e-11)[0])
     op.close()
 
 
