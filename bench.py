@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--grid", type=int, default=128)
@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--sample-iters", type=int, default=2)
+    ap.add_argument("--sample-iters", type=int, default=1)
     return ap.parse_args()
 
 
