@@ -153,6 +153,21 @@ KR_API kr_status kr_op_apply_reduce(kr_op op, int32_t adjoint, int32_t s, const 
 KR_API kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
                           void* stream);
 
+/* The reduction of kr_block_reduce without any device allocation by the library,
+ * for callers that cannot let a library allocate device memory (an application
+ * whose own pool allocator owns all device memory, or a latency-critical loop
+ * that cannot afford cudaMalloc's possible device synchronisation).  The paper
+ * has no counterpart: this is an interface variant, not a step of the method.
+ * Arguments and result as kr_block_reduce; out is caller-owned device memory.
+ * Limit: 1 <= s <= 16, otherwise KR_UNSUPPORTED before any GPU work.  The
+ * scratch (per-CTA partial sums) is a 1 MiB statically sized device array held
+ * by every GPU that loads the library until process exit.  The first call on a
+ * device looks up that array's device address once; make it before any stream
+ * capture.  All calls share the array (each fully overwrites what it reads, so
+ * nothing needs clearing); calls whose GPU work overlaps race on it. */
+KR_API kr_status kr_block_reduce_noalloc(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind,
+                                         double* out, void* stream);
+
 /* Thin QR of a device n x s block (Sec. 4, Eq. (QR)): Z = Q S, Q^H Q = I, S upper
  * triangular with real positive diagonal (CholQR2, shifted first pass when the
  * Gram matrix is not numerically positive definite).  Q (device n x s, may equal

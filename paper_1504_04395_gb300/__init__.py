@@ -85,6 +85,7 @@ SIGNATURES = {
     "kr_adjoint_solve": (_I32, [_P, _I32, _I32, _P, _P, ctypes.POINTER(KrOptions), _P, ctypes.POINTER(KrInfo)]),
     "kr_grad_values": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "kr_last_error": (ctypes.c_char_p, []),
+    "kr_block_reduce_noalloc": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
     "kr_profile_enable": (_I32, [_I32, _I32]),
     "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
 }
@@ -245,6 +246,21 @@ def kr_block_reduce(U, Y, kind="gram", stream=None):
     return out
 
 
+def kr_block_reduce_noalloc(U, Y, out, kind="gram", stream=None):
+    """kr_block_reduce into a caller-provided `out` with no device allocation by the library.
+
+    For callers whose device memory is owned by their own allocator or who cannot
+    afford an allocation in the call; s <= 16; see include/kr.h for the limits.
+    """
+    torch = _torch()
+    n, s = Y.shape
+    k = RED[kind] if isinstance(kind, str) else int(kind)
+    uptr = ctypes.c_void_p(0) if (U is None) else _dev_ptr(U, "U", torch.complex128)
+    _check(lib().kr_block_reduce_noalloc(n, s, uptr, _dev_ptr(Y, "Y", torch.complex128), k, _dev_ptr(out, "out"),
+                                         _stream(stream)))
+    return out
+
+
 def kr_thin_qr(Z, Q=None, stream=None):
     torch = _torch()
     n, s = Z.shape
@@ -367,5 +383,5 @@ __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
     "kr_op_create_csr", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
-    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "KERNEL_CLASSES",
+    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
 ]
