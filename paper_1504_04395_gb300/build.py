@@ -40,7 +40,8 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _digest() -> str:
+def source_digest() -> str:
+    """Hash of the CUDA / C sources and compile flags (identifies a kernel build on any host)."""
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):
         for f in sorted(os.listdir(d)):
@@ -48,8 +49,11 @@ def _digest() -> str:
                 h.update(f.encode())
                 h.update(fh.read())
     h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS).encode())
-    h.update(platform.machine().encode())
     return h.hexdigest()
+
+
+def _digest() -> str:
+    return hashlib.sha256((source_digest() + platform.machine()).encode()).hexdigest()
 
 
 def _compile(src: str) -> str:
