@@ -302,13 +302,17 @@ def gpu_arm(args):
                           "gbs": c["bytes"] / (c["ms"] / 1000.0) / 1e9 if c["ms"] > 0 else None}
                       for k, c in prof.items()},
     }
+    # DRAM traffic per launch from the committed ncu capture, only while the kernel sources
+    # are the ones that capture measured (otherwise null)
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         key = "%s_%d_%d" % (dom, args.grid, s)
-        if key in tr:
-            roofline["traffic"] = tr[key]
-    except Exception:
+        if key in tr and tr.get("source_digest") == build.source_digest():
+            roofline["traffic"] = tr[key]["bytes_per_launch"]
+            roofline["traffic_instance"] = tr[key]["instance"]
+            roofline["traffic_algorithmic_bytes"] = tr[key]["algorithmic_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
         pass
 
     # ---- end-to-end through the C interface with host buffers (pinned), copies in the timed region
