@@ -142,6 +142,23 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------------------
+# multi-rank aggregation (independent replicas: no data-path collective)
+# ------------------------------------------------------------------------------------------
+
+def aggregate_over_ranks(elapsed_s, units, dist=None, device="cpu"):
+    """Whole-job throughput: all ranks' units over the slowest rank's time (max over ranks)."""
+    if dist is None:
+        return units / elapsed_s, elapsed_s, units
+    import torch
+    t = torch.tensor([elapsed_s, float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tsum[1]) / float(tmax[0]), float(tmax[0]), float(tsum[1])
+
+
+# ------------------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
@@ -265,14 +282,9 @@ def gpu_arm(args):
     clk = clocks.stop()
     prof = kr.kr_profile_read(reset=True)
     kr.kr_profile_enable(False)
-    elapsed_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     units_rank = sum(s * info.iters for (_, info, _, _) in recs)
-    value = units_rank * world / (elapsed_ms / 1000.0)
-    ms_per_step = elapsed_ms / args.steps
+    value, elapsed_s, _ = aggregate_over_ranks(e0.elapsed_time(e1) / 1000.0, units_rank, dist, "cuda")
+    ms_per_step = 1000.0 * elapsed_s / args.steps
 
     per_method = {}
     for m in methods:
@@ -330,12 +342,8 @@ def gpu_arm(args):
                 _, info = kr.kr_solve(A, m, Bh, Xh, tol=args.tol, maxit=args.maxit, check_every=1)
                 e2e_units += s * info.iters
         barrier()
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": e2e_units * world / el, "unit": "RHS·iters/s",
+        e2e_value, _, _ = aggregate_over_ranks(time.perf_counter() - t0, e2e_units, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": "RHS·iters/s",
                "h2d_bytes_per_step": 2 * step_bytes * len(methods), "d2h_bytes_per_step": step_bytes * len(methods)}
 
     extras = {}
@@ -413,6 +421,20 @@ def bench_extras(kr, A, n, s, B, rp, ci, v, args, hbm_peak):
             times.append(time.perf_counter() - t0)
         res[name] = {"time_to_tol_ms": 1000 * statistics.median(times), "iters": inf.iters,
                      "outer": inf.outer_iters, "relres_true": inf.relres_true, "status": inf.status, "X": X.clone()}
+        # per kernel class rates of one more solve, CUDA events around every launch
+        X.zero_()
+        kr.kr_profile_read(reset=True)
+        kr.kr_profile_enable(True, time_kernels=True)
+        kr.kr_solve(A, "egl_bicg", Bd, X, tol=args.tol, maxit=2000, precision=prec, check_every=1)
+        torch.cuda.synchronize()
+        prof = kr.kr_profile_read(reset=True)
+        kr.kr_profile_enable(False)
+        res[name]["per_class"] = {
+            k: {"launches": c["launches"], "ms": c["ms"],
+                "gbs": c["bytes"] / (c["ms"] / 1000.0) / 1e9 if c["ms"] > 0 else None,
+                "hbm_frac": c["bytes"] / (c["ms"] / 1000.0) / 1e9 / hbm_peak if c["ms"] > 0 else None,
+                "tflops": c["flops"] / (c["ms"] / 1000.0) / 1e12 if c["ms"] > 0 else None}
+            for k, c in prof.items() if c["launches"]}
     diff = float(torch.linalg.norm(res["fp32_refine"]["X"] - res["fp64"]["X"]) / torch.linalg.norm(res["fp64"]["X"]))
     for r in res.values():
         r.pop("X")

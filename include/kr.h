@@ -122,6 +122,14 @@ KR_API void kr_options_default(kr_options* opt);
 KR_API kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                            const double* vals, int32_t device, kr_op* out);
 
+/* Replace the stored entries of A (same sparsity pattern, same order as given to
+ * kr_op_create_csr): vals[2*nnz] interleaved (re, im), a host pointer
+ * (on_device = 0) or a device pointer (on_device != 0).  A^H, the real/complex
+ * storage choice and the complex64 copy are rebuilt; cached workspace is kept.
+ * Used when A depends on parameters that are being optimised (differentiation
+ * through the solve). */
+KR_API kr_status kr_op_update_values(kr_op op, const double* vals, int32_t on_device);
+
 /* Release the operator, its device arrays and its cached workspace.  NULL is accepted. */
 KR_API kr_status kr_op_destroy(kr_op op);
 

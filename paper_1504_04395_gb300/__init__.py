@@ -76,6 +76,7 @@ SIGNATURES = {
     "kr_options_default": (None, [ctypes.POINTER(KrOptions)]),
     "kr_op_create_csr": (_I32, [_I64, _I64, _P, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_destroy": (_I32, [_P]),
+    "kr_op_update_values": (_I32, [_P, _P, _I32]),
     "kr_op_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
     "kr_op_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "kr_op_apply_reduce": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P]),
@@ -205,6 +206,21 @@ class Operator:
             self.close()
         except Exception:
             pass
+
+
+def kr_op_update_values(op: Operator, vals):
+    """Replace A's stored entries (CSR order of creation); vals: complex128 numpy array or tensor."""
+    torch = _torch()
+    if isinstance(vals, torch.Tensor):
+        v = vals.detach().to(torch.complex128).contiguous()
+        if v.is_cuda:
+            _check(lib().kr_op_update_values(op.handle, ctypes.c_void_p(v.data_ptr()), 1))
+            return
+        vals = v.numpy()
+    v = np.ascontiguousarray(vals, dtype=np.complex128)
+    if v.shape[0] != op.nnz:
+        raise ValueError("expected %d values, got %d" % (op.nnz, v.shape[0]))
+    _check(lib().kr_op_update_values(op.handle, ctypes.c_void_p(v.ctypes.data), 0))
 
 
 def kr_op_create_csr(n, rowptr, colidx, vals, device=None) -> Operator:
@@ -381,7 +397,7 @@ adjoint_solve = kr_adjoint_solve
 
 __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
-    "kr_op_create_csr", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
+    "kr_op_create_csr", "kr_op_update_values", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
     "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
 ]

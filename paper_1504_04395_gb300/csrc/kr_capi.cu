@@ -196,6 +196,22 @@ kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const 
   KR_API_END
 }
 
+kr_status kr_op_update_values(kr_op op, const double* vals, int32_t on_device) {
+  if (!op || (!vals && op->op.nnz > 0)) { set_error("op and vals must be non-NULL"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  if (on_device) {
+    KR_CUDA(cudaDeviceSynchronize());
+    KR_CUDA(cudaMemcpy(o.h_vals.data(), vals, sizeof(double) * 2 * o.nnz, cudaMemcpyDeviceToHost));
+  } else {
+    o.h_vals.assign(vals, vals + 2 * o.nnz);
+  }
+  rebuild_operator_values(o);
+  return KR_OK;
+  KR_API_END
+}
+
 kr_status kr_op_destroy(kr_op op) {
   if (!op) return KR_OK;
   KR_API_BEGIN

@@ -87,6 +87,7 @@ struct LinArgs {
   int nmat;
   const double2* mat[kMaxMat];   // device s x s (row-major) or s-vector (diagonal) coefficients
   int mat_is_diag[kMaxMat];
+  int mat_neg[kMaxMat];          // stored negated in shared memory
   Out o[kMaxOut];
 };
 

@@ -156,10 +156,12 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
   const int64_t n = a.n;
   const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
   C2<T> ysc = mk<T>((T)a.ay, (T)0);
+  const bool scaled = a.ys != nullptr || a.ay != 1.0;
   if (a.ys != nullptr) {
     C2<T> d = scalar_coef<T>(a.ys, a.ys_conj, a.ys_neg);
     ysc = mk<T>((T)a.ay * d.x, (T)a.ay * d.y);
   }
+  const T bz = (T)a.bz;
   Acc<T, G, NG> acc;
   acc_zero(acc);
   for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
@@ -184,11 +186,11 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
         }
       }
       if (act) {
-        y = cmul<T>(ysc, y);
+        if (scaled) y = cmul<T>(ysc, y);
         if (a.Z != nullptr) {
           const C2<T> z = a.Z[j * s + c];
-          y.x = fma((T)a.bz, z.x, y.x);
-          y.y = fma((T)a.bz, z.y, y.y);
+          y.x = fma(bz, z.x, y.x);
+          y.y = fma(bz, z.y, y.y);
         }
         if (a.Y != nullptr) a.Y[j * s + c] = y;
       }
@@ -229,7 +231,21 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
   C2<T>* Ms = reinterpret_cast<C2<T>*>(smem_raw);
   for (int m = 0; m < a.nmat; ++m) {
     const int cnt = a.mat_is_diag[m] ? s : ss;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) Ms[m * ss + i] = from_d2<T>(a.mat[m][i]);
+    const bool ng = a.mat_neg[m] != 0;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      C2<T> v = from_d2<T>(a.mat[m][i]);
+      if (ng) { v.x = -v.x; v.y = -v.y; }
+      Ms[m * ss + i] = v;
+    }
+  }
+  // scalar coefficients converted once per CTA (conjugation / negation applied)
+  __shared__ C2<T> Sc[kMaxOut * kMaxTerm];
+  if (threadIdx.x < kMaxOut * kMaxTerm) {
+    const int oi = threadIdx.x / kMaxTerm, ti = threadIdx.x % kMaxTerm;
+    C2<T> v = czero<T>();
+    if (oi < a.nout && ti < a.o[oi].nterm && a.o[oi].t[ti].coef_kind == COEF_SCALAR)
+      v = scalar_coef<T>(a.o[oi].t[ti].coef, a.o[oi].t[ti].conj, a.o[oi].t[ti].neg);
+    Sc[threadIdx.x] = v;
   }
   __syncthreads();
   C2<T>* red_sm = Ms + a.nmat * ss;
@@ -262,22 +278,22 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
             }
             if (t.xconj) x.y = -x.y;
             if (t.coef_kind == COEF_ONE) {
-              val = t.neg ? csub<T>(val, x) : cadd<T>(val, x);
+              if (ti == 0) val = t.neg ? mk<T>(-x.x, -x.y) : x;  // leading copy: no add to zero
+              else val = t.neg ? csub<T>(val, x) : cadd<T>(val, x);
             } else if (t.coef_kind == COEF_REAL) {
               val = cfmareal<T>((T)t.creal, x, val);
             } else if (t.coef_kind == COEF_SCALAR) {
-              val = cfma<T>(scalar_coef<T>(t.coef, t.conj, t.neg), x, val);
+              val = cfma<T>(Sc[oi * kMaxTerm + ti], x, val);
             } else if (t.coef_kind == COEF_DIAG) {
               C2<T> d = (c < s) ? Ms[t.coef_idx * ss + c] : czero<T>();
               if (t.conj) d.y = -d.y;
               if (t.neg) { d.x = -d.x; d.y = -d.y; }
               val = cfma<T>(d, x, val);
             } else {  // COEF_MAT: val += sum_a x[j][a] * M[a][c]  (or minus)
-              const C2<T>* M = Ms + t.coef_idx * ss;
-              const C2<T> xx = t.neg ? mk<T>(-x.x, -x.y) : x;
+              const C2<T>* M = Ms + t.coef_idx * ss;  // negation already folded into M
 #pragma unroll
               for (int q = 0; q < G; ++q) {
-                C2<T> xa = shfl<T>(xx, grpbase + q);
+                C2<T> xa = shfl<T>(x, grpbase + q);
                 if (q < s && c < s) val = cfma<T>(xa, M[q * s + c], val);
               }
             }

@@ -114,7 +114,7 @@ void launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* don
     for (int t = 0; t < q.nterm; ++t) {
       const Term& tm = q.t[t];
       switch (tm.coef_kind) {
-        case COEF_ONE: f += 2.0 * cnt; break;
+        case COEF_ONE: f += (t == 0 ? 0.0 : 2.0) * cnt; break;  // a leading copy is not arithmetic
         case COEF_REAL: f += 4.0 * cnt; break;
         case COEF_MAT: f += 8.0 * s * cnt; break;
         default: f += 8.0 * cnt; break;

@@ -138,6 +138,16 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
 
 }  // namespace
 
+void rebuild_operator_values(Operator& op) {
+  const bool had32 = op.have32;
+  op.A.free_all();
+  op.AH.free_all();
+  op.A32.free_all();
+  op.AH32.free_all();
+  op.have32 = false;
+  build_operator_device(op, had32);
+}
+
 void build_operator_device(Operator& op, bool want32) {
   const bool split = offdiag_real(op.n, op.h_rowptr, op.h_colidx, op.h_vals);
   op.real_offdiag = split ? 1 : 0;
@@ -254,11 +264,12 @@ struct Lin {
     a.o[o].nterm = 0;
     return o;
   }
-  int matidx(const double2* p, bool is_diag) {
+  int matidx(const double2* p, bool is_diag, bool neg) {
     for (int i = 0; i < a.nmat; ++i)
-      if (a.mat[i] == p) return i;
+      if (a.mat[i] == p && a.mat_neg[i] == (neg ? 1 : 0)) return i;
     a.mat[a.nmat] = p;
     a.mat_is_diag[a.nmat] = is_diag ? 1 : 0;
+    a.mat_neg[a.nmat] = neg ? 1 : 0;
     return a.nmat++;
   }
   void term(int o, int src_kind, const void* src, int reg, const Cf& c) {
@@ -272,7 +283,10 @@ struct Lin {
     t.neg = c.neg;
     t.conj = c.conj;
     t.xconj = c.xconj;
-    t.coef_idx = (c.kind == COEF_MAT || c.kind == COEF_DIAG) ? matidx(c.p, c.kind == COEF_DIAG) : 0;
+    // matrix negation is folded into the shared-memory copy; diagonal negation stays a flag
+    const bool mneg = c.kind == COEF_MAT && c.neg;
+    if (mneg) t.neg = 0;
+    t.coef_idx = (c.kind == COEF_MAT || c.kind == COEF_DIAG) ? matidx(c.p, c.kind == COEF_DIAG, mneg) : 0;
   }
   void blk(int o, const void* src, const Cf& c = Cf{}) { term(o, SRC_BLOCK, src, 0, c); }
   void vec(int o, const void* src, const Cf& c = Cf{}) { term(o, SRC_VEC, src, 0, c); }

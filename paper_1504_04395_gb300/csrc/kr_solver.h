@@ -38,6 +38,7 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
 
 double true_residual(Operator& op, int s, const void* B, const void* X, void* Rbuf, cudaStream_t st, bool adjoint);
 void ensure_orig_pattern(Operator& op);
+void rebuild_operator_values(Operator& op);
 void standalone_qr(Operator& op, Workspace& ws, int64_t n, int s, void* Q, cudaStream_t st);
 
 }  // namespace kr

@@ -60,9 +60,20 @@ def haar_links(dims, seed: int) -> np.ndarray:
     return Q * ph[..., None, :]
 
 
+def gamma5() -> np.ndarray:
+    """gamma_5 = gamma_1 gamma_2 gamma_3 gamma_4 (Hermitian, anticommutes with every gamma_mu)."""
+    return GAMMA[0] @ GAMMA[1] @ GAMMA[2] @ GAMMA[3]
+
+
 def lattice_csr(lat: Lattice4D, links: np.ndarray | None = None):
-    """Assemble the lattice operator as CSR (rowptr int64, colidx int32, vals complex128)."""
+    """Assemble the lattice operator as CSR (rowptr int64, colidx int32, vals complex128).
+
+    Only the 49 non-zeros of each row are generated: the diagonal, and for each of the
+    8 hops the 2 spin columns of (I -+ gamma_mu) times the 3 colour columns of the link.
+    """
     dims = tuple(int(L) for L in lat.dims)
+    if min(dims) < 3:
+        raise ValueError("every lattice extent must be >= 3 (forward and backward neighbours distinct)")
     sites = int(np.prod(dims))
     n = 12 * sites
     if links is None:
@@ -79,42 +90,34 @@ def lattice_csr(lat: Lattice4D, links: np.ndarray | None = None):
         return site + (c - coords[mu]) * strides[mu]
 
     eye = np.eye(4, dtype=np.complex128)
-    # blocks[k]: (neighbour site array, 12x12 block per site) for the 9 couplings
-    nbrs, blocks = [], []
+    cols = np.empty((sites, 4, 3, 49), dtype=np.int64)
+    vals = np.empty((sites, 4, 3, 49), dtype=np.complex128)
+    row_index = (site[:, None, None] * 4 + np.arange(4)[None, :, None]) * 3 + np.arange(3)[None, None, :]
+    cols[..., 0] = row_index
+    vals[..., 0] = 4.0 + lat.mass
+    k = 1
+    jj = np.arange(3)
     for mu in range(4):
-        fwd = shifted(mu, +1)
-        bwd = shifted(mu, -1)
-        Pm = -0.5 * (eye - GAMMA[mu])
-        Pp = -0.5 * (eye + GAMMA[mu])
-        Uf = links[mu]  # U_mu(x)
-        Ub = np.conj(np.swapaxes(links[mu][bwd], -1, -2))  # U_mu(x-mu)^H
-        nbrs.append(fwd)
-        blocks.append(np.einsum("ab,xij->xaibj", Pm, Uf).reshape(sites, 12, 12))
-        nbrs.append(bwd)
-        blocks.append(np.einsum("ab,xij->xaibj", Pp, Ub).reshape(sites, 12, 12))
-    nbrs.append(site)
-    blocks.append(np.broadcast_to((4.0 + lat.mass) * np.eye(12, dtype=np.complex128), (sites, 12, 12)))
-    # gather all (row, col, val), drop structural zeros, sort rows and columns
-    rows_l, cols_l, vals_l = [], [], []
-    r12 = np.arange(12)
-    for nb, blk in zip(nbrs, blocks):
-        rr = (site[:, None, None] * 12 + r12[None, :, None]) + 0 * r12[None, None, :]
-        cc = (nb[:, None, None] * 12 + r12[None, None, :]) + 0 * r12[None, :, None]
-        mask = blk != 0
-        rows_l.append(rr[mask])
-        cols_l.append(cc[mask])
-        vals_l.append(blk[mask])
-    rows = np.concatenate(rows_l)
-    cols = np.concatenate(cols_l)
-    vals = np.concatenate(vals_l)
-    order = np.lexsort((cols, rows))
-    rows, cols, vals = rows[order], cols[order], vals[order]
-    # merge duplicates (only possible when a dimension has extent <= 2)
-    key = rows * n + cols
-    uniq, start = np.unique(key, return_index=True)
-    if uniq.shape[0] != key.shape[0]:
-        vals = np.add.reduceat(vals, start)
-        rows, cols = rows[start], cols[start]
-    rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
-    return rowptr, cols.astype(np.int32), np.ascontiguousarray(vals)
+        for step in (+1, -1):
+            nb = shifted(mu, step)
+            P = -0.5 * (eye - step * GAMMA[mu])
+            if step > 0:
+                U = links[mu]                                            # U_mu(x)
+            else:
+                U = np.conj(np.swapaxes(links[mu][nb], -1, -2))          # U_mu(x - mu)^H
+            for a in range(4):
+                bs = [b for b in range(4) if P[a, b] != 0]
+                assert len(bs) == 2
+                for t, b in enumerate(bs):
+                    sl = slice(k + 3 * t, k + 3 * t + 3)
+                    cols[:, a, :, sl] = ((nb * 4 + b) * 3)[:, None, None] + jj[None, None, :]
+                    vals[:, a, :, sl] = P[a, b] * U
+            k += 6
+    assert k == 49
+    cols = cols.reshape(n, 49)
+    vals = vals.reshape(n, 49)
+    order = np.argsort(cols, axis=1, kind="stable")
+    cols = np.take_along_axis(cols, order, axis=1)
+    vals = np.take_along_axis(vals, order, axis=1)
+    rowptr = np.arange(0, 49 * (n + 1), 49, dtype=np.int64)
+    return rowptr, cols.reshape(-1).astype(np.int32), np.ascontiguousarray(vals.reshape(-1))
