@@ -296,7 +296,7 @@ def gpu_arm(args):
                          "rhs_iters_per_s": s * info.iters / (statistics.median(times) / 1000.0)}
 
     launches = int(sum(c["launches"] for c in prof.values()))
-    dom = max(("spmm", "lincomb"), key=lambda k: prof[k]["ms"])
+    dom = max(("spmm", "lincomb", "spmm_c64", "lincomb_c64"), key=lambda k: prof[k]["ms"])
     total_kernel_ms = sum(c["ms"] for c in prof.values())
     hbm_peak, hbm_src = measured_peaks()
     pd = prof[dom]

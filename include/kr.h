@@ -66,7 +66,8 @@ typedef enum {
   KR_BL_QMR = 7,          /* Bl-QMR with block products, no look-ahead (Sec. 2) */
   KR_GL_QMR = 8,          /* Gl-QMR (Sec. 2, global principle) */
   KR_EGL_QMR = 9,         /* eGl-QMR (Sec. 4) */
-  KR_LI_BICG = 10         /* Li-BiCG, Algorithm 1 (Sec. 2) */
+  KR_LI_BICG = 10,        /* Li-BiCG, Algorithm 1 (Sec. 2) */
+  KR_LI_BICGSTAB = 11     /* Li-BiCGStab: loop interchange (Sec. 2) applied to BiCGStab */
 } kr_method;
 
 typedef enum {
@@ -121,6 +122,17 @@ KR_API void kr_options_default(kr_options* opt);
  * malformed CSR (checked on the host), KR_OOM when device memory runs out. */
 KR_API kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                            const double* vals, int32_t device, kr_op* out);
+
+/* Matrix-free operator of a (2d+1)-point stencil on a d-dimensional grid (d = 1, 2, 3)
+ * with Dirichlet boundaries (the convection-diffusion discretisations of Sec. 5,
+ * Examples 1-3): unknown i = x_0 + N_0 x_1 + N_0 N_1 x_2 and
+ *   (A v)_i = c v_i + sum_a ( m_a v_{i - st_a} [x_a > 0] + p_a v_{i + st_a} [x_a < N_a - 1] ),
+ * st_a = N_0 ... N_{a-1}.  dims[d]: grid extents; coeffs[2 + 4d]: (re, im) of c, then for
+ * each axis a the pairs m_a, p_a.  No matrix is stored: a product reads only the
+ * vectors.  A^H uses the conjugated, mirrored coefficients.  kr_grad_values and
+ * kr_op_update_values need a CSR operator and return KR_UNSUPPORTED here. */
+KR_API kr_status kr_op_create_stencil(int32_t dim, const int64_t* dims, const double* coeffs, int32_t device,
+                                      kr_op* out);
 
 /* Replace the stored entries of A (same sparsity pattern, same order as given to
  * kr_op_create_csr): vals[2*nnz] interleaved (re, im), a host pointer
@@ -211,7 +223,9 @@ typedef enum {
   KR_K_REDUCE = 2,   /* fixed-order sums of per-CTA partial reductions */
   KR_K_COEF = 3,     /* one-CTA FP64 coefficient algebra (s x s solves, QR factors, rotations) */
   KR_K_OTHER = 4,    /* precision conversions, gradient */
-  KR_K_CLASSES = 5
+  KR_K_SPMM_C64 = 5,     /* block sparse products in complex64 (mixed-precision inner solves) */
+  KR_K_LINCOMB_C64 = 6,  /* row-local block updates in complex64 */
+  KR_K_CLASSES = 7
 } kr_kernel_class;
 
 typedef struct {

@@ -17,6 +17,7 @@ linear systems with many right-hand sides"):
 * eGl-BiCG     -- Sec. 4, Algorithm 4
 * Bl-BiCG-rQ   -- Sec. 4, Eqs. (QR), (newalpha)-(newbetahat), Algorithm 5
 * Li-BiCG      -- Sec. 2, Algorithm 1
+* Li-BiCGStab  -- the loop-interchange principle of Sec. 2 applied to BiCGStab
 * Gl-BiCGStab, Bl-BiCGStab, Bl-BiCGStab-rQ, Gl-QMR, eGl-QMR, Bl-QMR -- named
   but not written out in the paper (Secs. 2 and 4); the readings implemented
   here are stated in each function's docstring.
@@ -37,7 +38,7 @@ from .ops import (
     csr_matrix_from_arrays,
 )
 from .methods import (
-    METHODS, solve, gl_bicg, egl_bicg, bl_bicg, bl_bicg_rq, li_bicg,
+    METHODS, solve, gl_bicg, egl_bicg, bl_bicg, bl_bicg_rq, li_bicg, li_bicgstab,
     gl_bicgstab, bl_bicgstab, bl_bicgstab_rq, gl_qmr, egl_qmr, bl_qmr,
 )
 from .scalar import bicg_textbook, bicgstab_textbook
@@ -45,7 +46,7 @@ from .scalar import bicg_textbook, bicgstab_textbook
 __all__ = [
     "Status", "adjoint", "thin_qr", "frob", "trace_ip", "sum_ip", "gram", "spmm",
     "lu_solve", "csr_matrix_from_arrays", "METHODS", "solve",
-    "gl_bicg", "egl_bicg", "bl_bicg", "bl_bicg_rq", "li_bicg",
+    "gl_bicg", "egl_bicg", "bl_bicg", "bl_bicg_rq", "li_bicg", "li_bicgstab",
     "gl_bicgstab", "bl_bicgstab", "bl_bicgstab_rq", "gl_qmr", "egl_qmr", "bl_qmr",
     "bicg_textbook", "bicgstab_textbook",
 ]

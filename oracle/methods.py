@@ -290,6 +290,48 @@ def gl_bicgstab(A, AH, B, X0, Rt0, mon):
     return X
 
 
+def li_bicgstab(A, AH, B, X0, Rt0, mon):
+    """Li-BiCGStab: the loop-interchange principle of Sec. 2 (Algorithm 1) applied to BiCGStab.
+
+    s independent BiCGStab iterations sharing the block products A P and A S:
+      V = A P; alpha_i = rho_i / (rt_i^H v_i); S = R - V diag(alpha); T = A S;
+      omega_i = (t_i^H s_i) / (t_i^H t_i); X += P diag(alpha) + S diag(omega);
+      R = S - T diag(omega); beta_i = (rho_new_i / rho_i)(alpha_i / omega_i);
+      P = R + (P - V diag(omega)) diag(beta).
+    """
+    s = B.shape[1]
+    X = X0.copy()
+    R = B - spmm(A, X)
+    Rt = R.copy() if Rt0 is None else Rt0.copy()
+    P = R.copy()
+    mon.X = X
+    mon.begin(frob(R))
+    rho = np.array([np.vdot(Rt[:, i], R[:, i]) for i in range(s)])
+    while not mon.done:
+        V = spmm(A, P)
+        alpha = np.array([check_scalar(rho[i], np.vdot(Rt[:, i], V[:, i])) for i in range(s)])
+        S = R - V * alpha[None, :]
+        T = spmm(A, S)
+        omega = np.zeros(s, dtype=np.complex128)
+        for i in range(s):
+            tt = np.vdot(T[:, i], T[:, i])
+            ts = np.vdot(T[:, i], S[:, i])
+            if not (np.isfinite(tt) and np.isfinite(ts)):
+                raise FloatingPointError("non-finite omega")
+            omega[i] = 0.0 if tt == 0 else ts / tt
+        X = X + P * alpha[None, :] + S * omega[None, :]
+        R = S - T * omega[None, :]
+        mon.matvecs += 2 * s
+        mon.X = X
+        if mon.step(frob(R)):
+            break
+        rho_new = np.array([np.vdot(Rt[:, i], R[:, i]) for i in range(s)])
+        beta = np.array([check_scalar(rho_new[i], rho[i]) * check_scalar(alpha[i], omega[i]) for i in range(s)])
+        P = R + (P - V * omega[None, :]) * beta[None, :]
+        rho = rho_new
+    return X
+
+
 def bl_bicgstab(A, AH, B, X0, Rt0, mon):
     """Bl-BiCGStab (El Guennouni, Jbilou, Sadok), reading of Sec. 2:
 
@@ -603,6 +645,7 @@ METHODS = {
     "gl_qmr": gl_qmr,
     "egl_qmr": egl_qmr,
     "li_bicg": li_bicg,
+    "li_bicgstab": li_bicgstab,
 }
 
 

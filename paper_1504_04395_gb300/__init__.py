@@ -23,6 +23,7 @@ from .build import LIBPATH
 METHODS = {
     "bl_bicg": 0, "bl_bicg_rq": 1, "gl_bicg": 2, "egl_bicg": 3, "bl_bicgstab": 4,
     "bl_bicgstab_rq": 5, "gl_bicgstab": 6, "bl_qmr": 7, "gl_qmr": 8, "egl_qmr": 9, "li_bicg": 10,
+    "li_bicgstab": 11,
 }
 STATUS = {0: "OK", 1: "BREAKDOWN", 2: "DIVERGED", 3: "NAN", 4: "MAXIT", 5: "TIMEOUT", 6: "BAD_ARG",
           7: "OOM", 8: "CUDA_ERROR", 9: "UNSUPPORTED"}
@@ -66,7 +67,7 @@ class KrProfile(ctypes.Structure):
     ]
 
 
-KERNEL_CLASSES = ["spmm", "lincomb", "reduce", "coef", "other"]
+KERNEL_CLASSES = ["spmm", "lincomb", "reduce", "coef", "other", "spmm_c64", "lincomb_c64"]
 
 # exported symbols and their C signatures (must match include/kr.h)
 _P = ctypes.c_void_p
@@ -76,6 +77,7 @@ SIGNATURES = {
     "kr_options_default": (None, [ctypes.POINTER(KrOptions)]),
     "kr_op_create_csr": (_I32, [_I64, _I64, _P, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_destroy": (_I32, [_P]),
+    "kr_op_create_stencil": (_I32, [_I32, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_update_values": (_I32, [_P, _P, _I32]),
     "kr_op_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
     "kr_op_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
@@ -171,6 +173,27 @@ def method_id(method) -> int:
 
 class Operator:
     """Device copy of a CSR matrix A and its explicit adjoint (kr_op)."""
+
+    @classmethod
+    def stencil(cls, dims, centre, minus, plus, device=None):
+        """Matrix-free (2d+1)-point stencil (kr_op_create_stencil); minus/plus: one value per axis."""
+        torch = _torch()
+        if device is None:
+            device = torch.cuda.current_device()
+        d = len(dims)
+        coef = [complex(centre)]
+        for a in range(d):
+            coef += [complex(minus[a]), complex(plus[a])]
+        c = np.array([[z.real, z.imag] for z in coef], dtype=np.float64).reshape(-1)
+        dm = np.ascontiguousarray(dims, dtype=np.int64)
+        self = cls.__new__(cls)
+        self.n = int(np.prod(dims))
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check(lib().kr_op_create_stencil(d, dm.ctypes.data, c.ctypes.data, self.device, ctypes.byref(h)))
+        self._h = h
+        self.nnz = self.info()["nnz"]
+        return self
 
     def __init__(self, n, rowptr, colidx, vals, device=None):
         torch = _torch()

@@ -196,8 +196,58 @@ kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const 
   KR_API_END
 }
 
+kr_status kr_op_create_stencil(int32_t dim, const int64_t* dims, const double* coeffs, int32_t device, kr_op* out) {
+  if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }
+  *out = nullptr;
+  if (dim < 1 || dim > 3 || !dims || !coeffs) { set_error("dim must be 1, 2 or 3 with dims and coeffs"); return KR_BAD_ARG; }
+  int64_t n = 1;
+  for (int q = 0; q < dim; ++q) {
+    if (dims[q] < 1) { set_error("grid extents must be >= 1"); return KR_BAD_ARG; }
+    n *= dims[q];
+    if (n > 0x7fffffffLL) { set_error("grid too large"); return KR_BAD_ARG; }
+  }
+  for (int q = 0; q < 2 + 4 * dim; ++q)
+    if (!std::isfinite(coeffs[q])) { set_error("non-finite stencil coefficient"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { set_error("no CUDA device"); return KR_CUDA_ERROR; }
+  if (device < 0 || device >= ndev) { set_error("device ordinal out of range"); return KR_BAD_ARG; }
+  KR_CUDA(cudaSetDevice(device));
+  auto h = std::make_unique<kr_op_s>();
+  Operator& op = h->op;
+  op.device = device;
+  op.n = n;
+  StencilSpec& A = op.stA;
+  StencilSpec& AH = op.stAH;
+  A.d = AH.d = dim;
+  int64_t stride = 1, nnz = n;
+  bool real = true;
+  A.c = make_double2(coeffs[0], coeffs[1]);
+  AH.c = make_double2(coeffs[0], -coeffs[1]);
+  for (int q = 0; q < dim; ++q) {
+    A.dims[q] = AH.dims[q] = dims[q];
+    A.str[q] = AH.str[q] = stride;
+    nnz += 2 * (n - n / dims[q]);
+    stride *= dims[q];
+    A.m[q] = make_double2(coeffs[2 + 4 * q], coeffs[3 + 4 * q]);
+    A.p[q] = make_double2(coeffs[4 + 4 * q], coeffs[5 + 4 * q]);
+    real = real && coeffs[3 + 4 * q] == 0.0 && coeffs[5 + 4 * q] == 0.0;
+    // adjoint: (A^H)_{i, i+st} = conj(A_{i+st, i}) = conj(m), (A^H)_{i, i-st} = conj(p)
+    AH.p[q] = make_double2(A.m[q].x, -A.m[q].y);
+    AH.m[q] = make_double2(A.p[q].x, -A.p[q].y);
+  }
+  A.real = AH.real = real ? 1 : 0;
+  op.nnz = nnz;
+  op.real_offdiag = real ? 1 : 0;
+  KR_CUDA(cudaMallocHost(&op.pinned, 4096));
+  *out = h.release();
+  return KR_OK;
+  KR_API_END
+}
+
 kr_status kr_op_update_values(kr_op op, const double* vals, int32_t on_device) {
   if (!op || (!vals && op->op.nnz > 0)) { set_error("op and vals must be non-NULL"); return KR_BAD_ARG; }
+  if (op->op.stA.d > 0) { set_error("stencil operators have no CSR values"); return KR_UNSUPPORTED; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
@@ -240,10 +290,7 @@ static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const double* 
   Workspace& ws = get_workspace(o, s, sizeof(double2), 0, 0, 1);
   DevState h{};
   KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  const CsrDev<double>& M = op_mat<double>(o, adjoint != 0);
-  SpmmArgs<double> a{};
-  a.n = o.n; a.s = s; a.split = M.split; a.rowptr = M.rowptr; a.colidx = M.colidx; a.vals = M.vals;
-  a.offr = M.offr; a.diag = M.diag; a.nnz = M.nnz;
+  SpmmArgs<double> a = op_spmm_args<double>(o, adjoint != 0, s);
   a.V = reinterpret_cast<const double2*>(V);
   a.Y = reinterpret_cast<double2*>(Y);
   a.ay = 1.0;
@@ -455,6 +502,7 @@ kr_status kr_adjoint_solve(kr_op op, int32_t method, int32_t s, const double* G,
 
 kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double* X, double* dvals, void* stream) {
   if (!op || !Lambda || !X || !dvals || bad_s(s)) { set_error("invalid arguments"); return KR_BAD_ARG; }
+  if (op->op.stA.d > 0) { set_error("gradient on the CSR pattern needs a CSR operator"); return KR_UNSUPPORTED; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));

@@ -209,6 +209,49 @@ __global__ void __launch_bounds__(256) coef_kernel(CoefArgs a) {
       }
       break;
     }
+    // ------------------------------------------------------------ Li-BiCGStab (columnwise)
+    case PH_LS_ALPHA: {  // i0: rt_c^H v_c
+      if (threadIdx.x == 0) {
+        for (int c = 0; c < s; ++c) {
+          double2 al;
+          const int r = check_div(SLP(a, SL_TMP5)[c], red[a.i0 + c], &al);
+          if (r) { st->status = r; st->done = 1; break; }
+          SLP(a, SL_ALPHA)[c] = al;
+        }
+      }
+      break;
+    }
+    case PH_LS_OMEGA: {  // i0: s_c^H t_c (conjugated: t_c^H s_c), i1: t_c^H t_c
+      if (threadIdx.x == 0) {
+        for (int c = 0; c < s; ++c) {
+          const double2 ts = cj(red[a.i0 + c]);
+          const double tt = red[a.i1 + c].x;
+          if (!finite2(ts) || !isfinite(tt)) { st->status = ST_NAN; st->done = 1; break; }
+          const double2 om = tt == 0.0 ? make_double2(0.0, 0.0) : make_double2(ts.x / tt, ts.y / tt);
+          SLP(a, SL_OMEGA)[c] = om;
+          SLP(a, SL_NOMEGA)[c] = neg(om);
+        }
+      }
+      break;
+    }
+    case PH_LS_BETA: {  // i0: rt_c^H r_c (new), i1: ||R||^2
+      monitor(a, sqrt(red[a.i1].x));
+      if (is_done(st)) break;
+      if (threadIdx.x == 0) {
+        for (int c = 0; c < s; ++c) {
+          double2 b1, b2;
+          int r = check_div(red[a.i0 + c], SLP(a, SL_TMP5)[c], &b1);
+          if (!r) r = check_div(SLP(a, SL_ALPHA)[c], SLP(a, SL_OMEGA)[c], &b2);
+          if (r) { st->status = r; st->done = 1; break; }
+          const double2 be = cm(b1, b2);
+          SLP(a, SL_BETA)[c] = be;
+          SLP(a, SL_GAMMA)[c] = neg(cm(be, SLP(a, SL_OMEGA)[c]));
+        }
+        if (!st->done)
+          for (int c = 0; c < s; ++c) SLP(a, SL_TMP5)[c] = red[a.i0 + c];
+      }
+      break;
+    }
     // ------------------------------------------------------------ Bl-BiCG (Alg. 3)
     case PH_BL_G0: {
       from_red(SLP(a, SL_G), red + a.i0, ss);

@@ -54,6 +54,7 @@ enum Phase : int {
   PH_INIT = 0, PH_MONITOR,
   PH_SC_RHO0, PH_SC_ALPHA, PH_SC_BETA,                 // Gl/eGl-BiCG (scalar)
   PH_LI_RHO0, PH_LI_ALPHA, PH_LI_BETA,                 // Li-BiCG (diagonal)
+  PH_LS_ALPHA, PH_LS_OMEGA, PH_LS_BETA,                // Li-BiCGStab (diagonal)
   PH_BL_G0, PH_BL_ALPHA, PH_BL_BETA,                   // Bl-BiCG
   PH_QR1, PH_QR2,                                      // CholQR passes
   PH_RQ_INIT, PH_RQ_ALPHA, PH_RQ_C, PH_RQ_BETA,        // Bl-BiCG-rQ
@@ -93,10 +94,19 @@ struct CsrDev {
 
 struct Workspace;
 
+struct StencilSpec {
+  int d = 0;                 // 0: not a stencil operator
+  int real = 0;              // neighbour coefficients all real
+  int64_t dims[3] = {1, 1, 1};
+  int64_t str[3] = {0, 0, 0};
+  double2 c{}, m[3]{}, p[3]{};
+};
+
 struct Operator {
   int device = 0;
   int64_t n = 0, nnz = 0;
   int real_offdiag = 0;
+  StencilSpec stA, stAH;     // matrix-free operator (and its adjoint) when stA.d > 0
   CsrDev<double> A, AH;
   CsrDev<float> A32, AH32;
   bool have32 = false;
@@ -113,6 +123,10 @@ struct Operator {
 
 template <typename T>
 const CsrDev<T>& op_mat(const Operator& op, bool adjoint);
+
+// product arguments for op(A) (CSR or stencil), without V / Y / Z / scaling
+template <typename T>
+SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s);
 
 void build_operator_device(Operator& op, bool want32);
 

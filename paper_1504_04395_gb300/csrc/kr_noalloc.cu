@@ -105,6 +105,7 @@ extern "C" kr_status kr_block_reduce_noalloc(int64_t n, int32_t s, const double*
   rs.r[0].U = U;
   rs.nslots = kind == KR_RED_GRAM ? s * s : 1;
   rs.partials = scratch;
+  resolve_sources(a, rs);  // two operands at most: always fits
   int grid = row_grid(n, s);
   if (grid > kNoAllocMaxCtas) grid = kNoAllocMaxCtas;
   const bool gram = kind == KR_RED_GRAM;

@@ -7,7 +7,9 @@
 
 namespace kr {
 
-enum KernelClass : int { KC_SPMM = 0, KC_LINCOMB = 1, KC_REDUCE = 2, KC_COEF = 3, KC_OTHER = 4 };
+enum KernelClass : int {
+  KC_SPMM = 0, KC_LINCOMB = 1, KC_REDUCE = 2, KC_COEF = 3, KC_OTHER = 4, KC_SPMM32 = 5, KC_LINCOMB32 = 6
+};
 
 struct ProfToken {
   int cls = 0;

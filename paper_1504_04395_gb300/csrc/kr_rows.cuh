@@ -20,6 +20,7 @@ struct RedSpec {
   int kind;        // RedKind
   int ysrc;        // which computed value is Y (linear combination: output index; SpMM: 0)
   int ureg;        // >= 0: U is computed output ureg of this launch; -1: U is read from memory
+  int usrc;        // linear combination: operand index of a memory U (-1: none)
   int gacc;        // accumulator index for RED_GRAM
   const void* U;   // memory operand: n x s block (GRAM, TRACE) or n-vector (SUMV, GRAMV)
   int slot;        // first slot of this reduction in a CTA's partial record
@@ -53,6 +54,14 @@ struct SpmmArgs {
   const double2* ys;         // optional device scalar multiplying ay (complex)
   int ys_conj, ys_neg;
   int64_t nnz;               // stored entries (host-side bookkeeping for the launch profile)
+  // matrix-free (2d+1)-point stencil with Dirichlet boundaries (nst = d > 0 replaces the CSR):
+  // y_j = c V_j + sum_a m_a V_{j - st_a} [x_a > 0] + p_a V_{j + st_a} [x_a < N_a - 1]
+  int nst;
+  int sreal;                 // all neighbour coefficients real
+  int64_t sdims[3];
+  int64_t sstr[3];
+  double2 sc;                // centre
+  double2 sm[3], sp[3];      // minus / plus neighbour along each axis
 };
 
 // ---------------------------------------------------------------------------------------
@@ -63,7 +72,7 @@ enum CoefKind : int { COEF_ONE = 0, COEF_SCALAR = 1, COEF_MAT = 2, COEF_DIAG = 3
 
 struct Term {
   int src_kind;        // SrcKind
-  int src_reg;         // SRC_REG: index of an earlier output
+  int src_reg;         // SRC_REG: index of an earlier output; SRC_BLOCK / SRC_VEC: operand index
   const void* src;     // SRC_BLOCK / SRC_VEC pointer
   int coef_kind;       // CoefKind
   int coef_idx;        // COEF_MAT / COEF_DIAG: index into the launch's matrix table
@@ -80,15 +89,50 @@ struct Out {
   Term t[kMaxTerm];
 };
 
+constexpr int kMaxSrc = 10;    // distinct memory operands of one linear-combination launch
+
 struct LinArgs {
   int64_t n;
   int s;
   int nout;
   int nmat;
+  int nsrc;                      // distinct memory operands, all loaded before any store
+  const void* src[kMaxSrc];
+  int src_vec[kMaxSrc];          // n-vector (1) or n x s block (0)
   const double2* mat[kMaxMat];   // device s x s (row-major) or s-vector (diagonal) coefficients
   int mat_is_diag[kMaxMat];
   int mat_neg[kMaxMat];          // stored negated in shared memory
   Out o[kMaxOut];
 };
+
+// Fill the launch's operand table: every memory source of a term and every memory U of a
+// reduction gets an index (equal pointers share one); returns false if there are more than
+// kMaxSrc distinct operands.
+inline bool resolve_sources(LinArgs& a, RedSet& rs) {
+  a.nsrc = 0;
+  auto add = [&](const void* p, int vec) -> int {
+    for (int i = 0; i < a.nsrc; ++i)
+      if (a.src[i] == p && a.src_vec[i] == vec) return i;
+    if (a.nsrc >= kMaxSrc) return -1;
+    a.src[a.nsrc] = p;
+    a.src_vec[a.nsrc] = vec;
+    return a.nsrc++;
+  };
+  for (int o = 0; o < a.nout; ++o)
+    for (int t = 0; t < a.o[o].nterm; ++t) {
+      Term& tm = a.o[o].t[t];
+      if (tm.src_kind == SRC_REG) continue;
+      tm.src_reg = add(tm.src, tm.src_kind == SRC_VEC ? 1 : 0);
+      if (tm.src_reg < 0) return false;
+    }
+  for (int i = 0; i < rs.nred; ++i) {
+    RedSpec& r = rs.r[i];
+    r.usrc = -1;
+    if (r.ureg >= 0 || r.U == nullptr) continue;
+    r.usrc = add(r.U, (r.kind == RED_SUMV || r.kind == RED_GRAMV) ? 1 : 0);
+    if (r.usrc < 0) return false;
+  }
+  return true;
+}
 
 }  // namespace kr

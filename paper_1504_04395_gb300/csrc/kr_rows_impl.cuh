@@ -134,6 +134,15 @@ __device__ __forceinline__ C2<T> pick(const C2<T> (&o)[kMaxOut], int r) {
 }
 
 template <typename T>
+__device__ __forceinline__ C2<T> pick_src(const C2<T> (&x)[kMaxSrc], int r) {
+  C2<T> v = x[0];
+#pragma unroll
+  for (int i = 1; i < kMaxSrc; ++i)
+    if (r == i) v = x[i];
+  return v;
+}
+
+template <typename T>
 __device__ __forceinline__ C2<T> scalar_coef(const double2* p, int conj, int neg) {
   double2 d = *p;
   if (conj) d.y = -d.y;
@@ -169,20 +178,95 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
     const bool rowok = j < n;
     const bool act = rowok && c < s;
     C2<T> y = czero<T>();
-    if (rowok) {
+    if (rowok && a.nst > 0) {
+      // matrix-free stencil, same summation order as the real-off-diagonal CSR storage:
+      // centre, then -axis d-1 .. -axis 0, then +axis 0 .. +axis d-1
+      int64_t xc[3];
+      int64_t rem = j;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
+      }
+      C2<T> xs[7];
+      bool hs[7];
+      hs[0] = true;
+      xs[0] = act ? a.V[j * s + c] : czero<T>();
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int qa = 2 - q;  // descending axes for the minus side
+        const bool okm = qa < a.nst && xc[qa] > 0;
+        hs[1 + q] = okm;
+        xs[1 + q] = (act && okm) ? a.V[(j - a.sstr[qa]) * s + c] : czero<T>();
+        const bool okp = q < a.nst && xc[q] < a.sdims[q] - 1;
+        hs[4 + q] = okp;
+        xs[4 + q] = (act && okp) ? a.V[(j + a.sstr[q]) * s + c] : czero<T>();
+      }
+      if (act) {
+        y = cmul<T>(mk<T>((T)a.sc.x, (T)a.sc.y), xs[0]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int qa = 2 - q;
+          if (hs[1 + q]) {
+            if (a.sreal) y = cfmareal<T>((T)a.sm[qa].x, xs[1 + q], y);
+            else y = cfma<T>(mk<T>((T)a.sm[qa].x, (T)a.sm[qa].y), xs[1 + q], y);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (hs[4 + q]) {
+            if (a.sreal) y = cfmareal<T>((T)a.sp[q].x, xs[4 + q], y);
+            else y = cfma<T>(mk<T>((T)a.sp[q].x, (T)a.sp[q].y), xs[4 + q], y);
+          }
+        }
+        if (scaled) y = cmul<T>(ysc, y);
+        if (a.Z != nullptr) {
+          const C2<T> z = a.Z[j * s + c];
+          y.x = fma(bz, z.x, y.x);
+          y.y = fma(bz, z.y, y.y);
+        }
+        if (a.Y != nullptr) a.Y[j * s + c] = y;
+      }
+    } else if (rowok) {
       const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
+      // batches of kBatch entries: all index, value and gathered-row loads of a batch are
+      // issued before its FMAs, so several neighbour rows are in flight per thread
+      constexpr int kBatch = sizeof(T) == 4 ? 4 : 1;
       if (a.split) {
         if (act) y = cmul<T>(a.diag[j], a.V[j * s + c]);
-        for (int64_t k = k0; k < k1; ++k) {
-          const T v = a.offr[k];
-          const int64_t col = a.colidx[k];
-          if (act) y = cfmareal<T>(v, a.V[col * s + c], y);
+        for (int64_t k = k0; k < k1; k += kBatch) {
+          int32_t col[kBatch];
+          T v[kBatch];
+          C2<T> x[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const bool in = k + u < k1;
+            col[u] = in ? a.colidx[k + u] : 0;
+            v[u] = in ? a.offr[k + u] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u)
+            x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u)
+            if (act && k + u < k1) y = cfmareal<T>(v[u], x[u], y);
         }
       } else {
-        for (int64_t k = k0; k < k1; ++k) {
-          const C2<T> v = a.vals[k];
-          const int64_t col = a.colidx[k];
-          if (act) y = cfma<T>(v, a.V[col * s + c], y);
+        for (int64_t k = k0; k < k1; k += kBatch) {
+          int32_t col[kBatch];
+          C2<T> v[kBatch];
+          C2<T> x[kBatch];
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u) {
+            const bool in = k + u < k1;
+            col[u] = in ? a.colidx[k + u] : 0;
+            v[u] = in ? a.vals[k + u] : czero<T>();
+          }
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u)
+            x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
+#pragma unroll
+          for (int u = 0; u < kBatch; ++u)
+            if (act && k + u < k1) y = cfma<T>(v[u], x[u], y);
         }
       }
       if (act) {
@@ -202,7 +286,8 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
           const RedSpec& r = rs.r[ri];
           C2<T> u = czero<T>();
           if (r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT) {
-            if (act) u = reinterpret_cast<const C2<T>*>(r.U)[j * s + c];
+            // U == nullptr: reduction of the product with itself (Y^H Y)
+            if (act) u = (r.U != nullptr) ? reinterpret_cast<const C2<T>*>(r.U)[j * s + c] : y;
           } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
             if (rowok) u = reinterpret_cast<const C2<T>*>(r.U)[j];
           }
@@ -256,6 +341,20 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
+    // every memory operand of the row is loaded before any output is stored (outputs may
+    // alias operands, so the compiler could not hoist these loads itself)
+    C2<T> xin[kMaxSrc];
+#pragma unroll
+    for (int q = 0; q < kMaxSrc; ++q) {
+      xin[q] = czero<T>();
+      if (q < a.nsrc) {
+        if (a.src_vec[q]) {
+          if (rowok) xin[q] = reinterpret_cast<const C2<T>*>(a.src[q])[j];
+        } else if (act) {
+          xin[q] = reinterpret_cast<const C2<T>*>(a.src[q])[j * s + c];
+        }
+      }
+    }
     C2<T> o[kMaxOut];
 #pragma unroll
     for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();
@@ -268,14 +367,7 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
         for (int ti = 0; ti < kMaxTerm; ++ti) {
           if (ti < out.nterm) {
             const Term& t = out.t[ti];
-            C2<T> x = czero<T>();
-            if (t.src_kind == SRC_REG) {
-              x = pick<T>(o, t.src_reg);
-            } else if (t.src_kind == SRC_BLOCK) {
-              if (act) x = reinterpret_cast<const C2<T>*>(t.src)[j * s + c];
-            } else {
-              if (rowok) x = reinterpret_cast<const C2<T>*>(t.src)[j];
-            }
+            C2<T> x = (t.src_kind == SRC_REG) ? pick<T>(o, t.src_reg) : pick_src<T>(xin, t.src_reg);
             if (t.xconj) x.y = -x.y;
             if (t.coef_kind == COEF_ONE) {
               if (ti == 0) val = t.neg ? mk<T>(-x.x, -x.y) : x;  // leading copy: no add to zero
@@ -317,10 +409,8 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
           C2<T> u = czero<T>();
           if (r.ureg >= 0) {
             u = pick<T>(o, r.ureg);
-          } else if (r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT) {
-            if (act) u = reinterpret_cast<const C2<T>*>(r.U)[j * s + c];
-          } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
-            if (rowok) u = reinterpret_cast<const C2<T>*>(r.U)[j];
+          } else if (r.usrc >= 0) {
+            u = pick_src<T>(xin, r.usrc);
           }
           red_add<T, G, NG>(r, ri, acc, y, u, s, grpbase);
         }

@@ -56,7 +56,7 @@ static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int grid, cons
 
 template <typename T>
 void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
-  ProfToken tk = prof_begin(KC_SPMM, st);
+  ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM, st);
   spmm_dispatch<T>(a, rs, grid, done, st);
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s, nnz = (double)a.nnz;
@@ -64,7 +64,8 @@ void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* do
   if (a.ys != nullptr || a.ay != 1.0) f += 6.0 * s * n;
   if (a.Z != nullptr) f += 4.0 * s * n;
   f += red_flops(rs, a.n, a.s);
-  double b = 8.0 * (n + 1) + 4.0 * nnz + (a.split ? sizeof(T) * nnz + E * n : E * nnz);
+  double b = a.nst > 0 ? 0.0 : 8.0 * (n + 1) + 4.0 * nnz + (a.split ? sizeof(T) * nnz + E * n : E * nnz);
+  if (a.nst > 0 && !a.sreal) f = s * 8.0 * (nnz + n);
   b += E * n * s;
   if (a.Y != nullptr) b += E * n * s;
   if (a.Z != nullptr) b += E * n * s;
@@ -100,8 +101,11 @@ template <typename T>
 static void lin_dispatch(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
 
 template <typename T>
-void launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
-  ProfToken tk = prof_begin(KC_LINCOMB, st);
+void launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int* done, cudaStream_t st) {
+  LinArgs a = a_in;
+  RedSet rs = rs_in;
+  if (!resolve_sources(a, rs)) throw CudaError{cudaErrorInvalidValue, "lincomb: too many distinct operands"};
+  ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_LINCOMB32 : KC_LINCOMB, st);
   lin_dispatch<T>(a, rs, grid, done, st);
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s;

@@ -53,6 +53,40 @@ const CsrDev<double>& op_mat<double>(const Operator& op, bool adjoint) { return 
 template <>
 const CsrDev<float>& op_mat<float>(const Operator& op, bool adjoint) { return adjoint ? op.AH32 : op.A32; }
 
+template <typename T>
+SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s) {
+  SpmmArgs<T> a{};
+  a.n = op.n;
+  a.s = s;
+  a.ay = 1.0;
+  if (op.stA.d > 0) {
+    const StencilSpec& st = adjoint ? op.stAH : op.stA;
+    a.nst = st.d;
+    a.sreal = st.real;
+    for (int q = 0; q < 3; ++q) {
+      a.sdims[q] = st.dims[q];
+      a.sstr[q] = st.str[q];
+      a.sm[q] = st.m[q];
+      a.sp[q] = st.p[q];
+    }
+    a.sc = st.c;
+    a.split = 1;  // profile accounting: real neighbours
+    a.nnz = op.nnz - op.n;
+    return a;
+  }
+  const CsrDev<T>& M = op_mat<T>(op, adjoint);
+  a.split = M.split;
+  a.rowptr = M.rowptr;
+  a.colidx = M.colidx;
+  a.vals = M.vals;
+  a.offr = M.offr;
+  a.diag = M.diag;
+  a.nnz = M.nnz;
+  return a;
+}
+template SpmmArgs<double> op_spmm_args<double>(const Operator&, bool, int);
+template SpmmArgs<float> op_spmm_args<float>(const Operator&, bool, int);
+
 namespace {
 
 struct HostCsr {
@@ -149,6 +183,7 @@ void rebuild_operator_values(Operator& op) {
 }
 
 void build_operator_device(Operator& op, bool want32) {
+  if (op.stA.d > 0) return;  // matrix-free: nothing to upload
   const bool split = offdiag_real(op.n, op.h_rowptr, op.h_colidx, op.h_vals);
   op.real_offdiag = split ? 1 : 0;
   HostCsr t = transpose_conj(op.n, op.h_rowptr, op.h_colidx, op.h_vals);
@@ -316,16 +351,8 @@ struct Engine {
   // Y = ay op(A) V + bz Z, op(A) = A or A^H, with fused reductions; returns red offset
   int spmm(bool adjA, int sdim, const void* V, void* Y, Reds r = Reds{}, const void* Z = nullptr, double ay = 1.0,
            double bz = 0.0, const double2* ys = nullptr, bool ysconj = false, bool ysneg = false) {
-    const CsrDev<T>& M = op_mat<T>(op, adjA != swap);
-    SpmmArgs<T> a{};
+    SpmmArgs<T> a = op_spmm_args<T>(op, adjA != swap, sdim);
     a.n = n;
-    a.s = sdim;
-    a.split = M.split;
-    a.rowptr = M.rowptr;
-    a.colidx = M.colidx;
-    a.vals = M.vals;
-    a.offr = M.offr;
-    a.diag = M.diag;
     a.V = reinterpret_cast<const C2<T>*>(V);
     a.Y = reinterpret_cast<C2<T>*>(Y);
     a.Z = reinterpret_cast<const C2<T>*>(Z);
@@ -334,7 +361,6 @@ struct Engine {
     a.ys = ys;
     a.ys_conj = ysconj;
     a.ys_neg = ysneg;
-    a.nnz = M.nnz;
     r.rs.partials = ws.partials;
     const int grid = row_grid(n, sdim);
     if (count_grams(r.rs) <= ng_capacity(threads_per_row(sdim))) {
@@ -697,6 +723,59 @@ void run_li_bicg(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
     U.blk(oph, Rh);
     U.blk(oph, Ph, dg(E.slot(SL_BETA), true));
     E.lin(U);
+    if (poll(it + 1)) break;
+  }
+}
+
+template <typename T>
+void run_li_bicgstab(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
+  Engine<T>& E = c.E;
+  void *R = E.blk(0), *Rt = E.blk(1), *P = E.blk(2), *V = E.blk(3), *S = E.blk(4), *T_ = E.blk(5);
+  init_residual(E, c.B, c.X, R);
+  make_shadow(E, R, Rt, c.shadow_mode, c.shadow);
+  {
+    Lin L(E.n, E.s);
+    const int op_ = L.out(P);
+    L.blk(op_, R);
+    Reds r;
+    const int sl = r.add(RED_CDOT, op_, -1, Rt, E.s);  // rt_c^H r_c
+    const int off = E.lin(L, r);
+    E.coef(PH_LI_RHO0, off + sl);
+  }
+  for (int it = 0; it < maxit; ++it) {
+    E.red_top = 0;
+    Reds r1;
+    const int s1 = r1.add(RED_CDOT, 0, -1, Rt, E.s);  // rt_c^H v_c
+    const int o1 = E.spmm(false, E.s, P, V, r1);
+    E.coef(PH_LS_ALPHA, o1 + s1);
+    Lin L(E.n, E.s);
+    const int os = L.out(S);
+    L.blk(os, R);
+    L.blk(os, V, dg(E.slot(SL_ALPHA), false, true));
+    E.lin(L);
+    Reds r2;
+    const int s2 = r2.add(RED_CDOT, 0, -1, S, E.s);        // s_c^H t_c
+    const int s3 = r2.add(RED_CDOT, 0, -1, nullptr, E.s);  // t_c^H t_c
+    const int o2 = E.spmm(false, E.s, S, T_, r2);
+    E.coef(PH_LS_OMEGA, o2 + s2, o2 + s3);
+    Lin U(E.n, E.s);
+    const int ox = U.out(c.X), orr = U.out(R);
+    U.blk(ox, c.X);
+    U.blk(ox, P, dg(E.slot(SL_ALPHA)));
+    U.blk(ox, S, dg(E.slot(SL_OMEGA)));
+    U.blk(orr, S);
+    U.blk(orr, T_, dg(E.slot(SL_NOMEGA)));
+    Reds r3;
+    const int s4 = r3.add(RED_CDOT, orr, -1, Rt, E.s);
+    const int s5 = r3.add(RED_NORM2, orr, -1, nullptr, E.s);
+    const int o3 = E.lin(U, r3);
+    E.coef(PH_LS_BETA, o3 + s4, o3 + s5);
+    Lin W(E.n, E.s);
+    const int op_ = W.out(P);
+    W.blk(op_, R);
+    W.blk(op_, P, dg(E.slot(SL_BETA)));
+    W.blk(op_, V, dg(E.slot(SL_GAMMA)));  // -beta omega
+    E.lin(W);
     if (poll(it + 1)) break;
   }
 }
@@ -1223,6 +1302,7 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
     case KRM_GL_BICG: run_gl_bicg<T>(c, in.maxit, poll); break;
     case KRM_EGL_BICG: run_egl_bicg<T>(c, in.maxit, poll); break;
     case KRM_LI_BICG: run_li_bicg<T>(c, in.maxit, poll); break;
+    case KRM_LI_BICGSTAB: run_li_bicgstab<T>(c, in.maxit, poll); break;
     case KRM_BL_BICG: run_bl_bicg<T>(c, in.maxit, poll); break;
     case KRM_BL_BICG_RQ: run_bl_bicg_rq<T>(c, in.maxit, poll); break;
     case KRM_GL_BICGSTAB: run_gl_bicgstab<T>(c, in.maxit, poll); break;

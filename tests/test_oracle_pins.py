@@ -20,7 +20,7 @@ from workloads import ConvDiff, convdiff_csr, gaussian_block, grid_nnz, Lattice4
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 BICG_LIKE = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "li_bicg"]
-STAB_LIKE = ["bl_bicgstab", "bl_bicgstab_rq", "gl_bicgstab"]
+STAB_LIKE = ["bl_bicgstab", "bl_bicgstab_rq", "gl_bicgstab", "li_bicgstab"]
 QMR_LIKE = ["gl_qmr", "egl_qmr", "bl_qmr"]
 ALL = BICG_LIKE + STAB_LIKE + QMR_LIKE
 
@@ -257,6 +257,15 @@ def test_global_bicg_petrov_galerkin():
         r = oracle.solve("gl_bicg", A, B, tol=0.0, maxit=k)
         x_pg = _pg_iterate(K, vec(B)[:, None], vec(B)[:, None], k)[:, 0]
         assert rel(vec(r.X), x_pg) < 1e-9
+
+
+def test_li_bicgstab_is_columnwise_bicgstab():
+    """Li-BiCGStab: column i is BiCGStab for A x_i = b_i (loop interchange, Sec. 2)."""
+    A, B = problem(N=7, s=3, shift=0.3j)
+    r = oracle.solve("li_bicgstab", A, B, tol=0.0, maxit=9)
+    for i in range(3):
+        ref = oracle.bicgstab_textbook(A, B[:, i], iters=9)
+        assert rel(r.X[:, i], ref["x"][9]) < 1e-10
 
 
 def test_li_bicg_is_columnwise_bicg():

@@ -34,6 +34,11 @@ GAMMA = np.array(
 )
 
 
+# mass giving sigma_max / sigma_min ~ 1e3 (964 on the 4^4 lattice with seed 0), from
+# python -m workloads.calibrate_lattice (dense SVD on the CPU)
+LATTICE_MASS_KAPPA_1E3 = -2.05
+
+
 @dataclass(frozen=True)
 class Lattice4D:
     dims: tuple  # (L0, L1, L2, L3), axis 0 fastest
