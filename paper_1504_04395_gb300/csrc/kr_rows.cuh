@@ -129,7 +129,16 @@ inline bool resolve_sources(LinArgs& a, RedSet& rs) {
     RedSpec& r = rs.r[i];
     r.usrc = -1;
     if (r.ureg >= 0 || r.U == nullptr) continue;
-    r.usrc = add(r.U, (r.kind == RED_SUMV || r.kind == RED_GRAMV) ? 1 : 0);
+    const int vec = (r.kind == RED_SUMV || r.kind == RED_GRAMV) ? 1 : 0;
+    // a U that this launch writes is reduced with its new value (the output's register)
+    int written = -1;
+    for (int o = 0; o < a.nout; ++o)
+      if (a.o[o].dst == r.U && a.o[o].is_vec == vec) written = o;
+    if (written >= 0) {
+      r.ureg = written;
+      continue;
+    }
+    r.usrc = add(r.U, vec);
     if (r.usrc < 0) return false;
   }
   return true;

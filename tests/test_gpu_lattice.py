@@ -1,7 +1,7 @@
 """4D lattice operator at full size (GPU): the stand-in for Example 4 (configs 3 and 4).
 
-16^4 sites x 12 unknowns (n = 786,432, 49 non-zeros per row, mass calibrated to a
-condition number of about 1e3), s = 12 point sources and s = 12 Gaussian right-hand
+16^4 sites x 12 unknowns (n = 786,432, 49 non-zeros per row, mass chosen so the
+spectrum stays in the right half-plane), s = 12 point sources and s = 12 Gaussian right-hand
 sides, eGl-BiCG, eGl-QMR and Bl-BiCGStab-rQ to 1e-8: convergence with the true
 residual recomputed in FP64, and the first iterations against the oracle on the same
 full-size inputs.  Mixed precision (complex64 inner solves, FP64 defect correction)
@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
 from workloads import Lattice4D, gaussian_block, lattice_csr, point_sources  # noqa: E402
-from workloads.lattice import LATTICE_MASS_KAPPA_1E3  # noqa: E402
+from workloads.lattice import LATTICE_MASS  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -27,7 +27,7 @@ def lat():
     build.build()
     import paper_1504_04395_gb300 as kr
     kr.load_library()
-    L = Lattice4D((16, 16, 16, 16), LATTICE_MASS_KAPPA_1E3, seed=0)
+    L = Lattice4D((16, 16, 16, 16), LATTICE_MASS, seed=0)
     rp, ci, v = lattice_csr(L)
     op = kr.Operator(L.n, rp, ci, v)
     yield kr, L, rp, ci, v, op
