@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--config4", action="store_true",
+                    help="mixed precision vs FP64 on the 4D lattice (24^4 x 12, s = 32, eGl-BiCG to 1e-10)")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=1)
     return ap.parse_args()
@@ -444,10 +446,62 @@ def bench_extras(kr, A, n, s, B, rp, ci, v, args, hbm_peak):
     return out
 
 
+def config4(args):
+    """Mixed precision (complex64 inner solves, tol 1e-4, FP64 defect correction to 1e-10) against the
+    pure-FP64 GPU path on the 4D lattice operator, 24^4 sites x 12 dof (n = 3,981,312, 49 entries per
+    row), s = 32 Gaussian right-hand sides, eGl-BiCG (Algorithm 4)."""
+    import torch
+    from workloads import Lattice4D, gaussian_block, lattice_csr
+    from workloads.lattice import LATTICE_MASS
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as kr
+    L = args.grid if args.grid != 128 else 24
+    s = args.s if args.s != 8 else 32
+    lat = Lattice4D((L,) * 4, LATTICE_MASS, seed=0)
+    t0 = time.perf_counter()
+    rp, ci, v = lattice_csr(lat)
+    gen_s = time.perf_counter() - t0
+    A = kr.Operator(lat.n, rp, ci, v)
+    B = torch.from_numpy(gaussian_block(lat.n, s, seed=32)).cuda()
+    hbm_peak, _ = measured_peaks()
+    out = {"workload": "4D lattice %d^4 x 12 (n=%d, nnz=%d), m=%.2f, s=%d Gaussian RHS, eGl-BiCG to 1e-10"
+                       % (L, lat.n, len(ci), LATTICE_MASS, s), "generation_s": gen_s}
+    X = {}
+    for prec, name in ((kr.FP64, "fp64"), (kr.FP32_REFINE, "fp32_refine")):
+        Xd = torch.zeros_like(B)
+        kr.kr_profile_read(reset=True)
+        kr.kr_profile_enable(True, time_kernels=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, inf = kr.kr_solve(A, "egl_bicg", B, Xd, tol=1e-10, maxit=5000, precision=prec, inner_tol=1e-4,
+                             check_every=8)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        prof = kr.kr_profile_read(reset=True)
+        kr.kr_profile_enable(False)
+        X[name] = Xd
+        out[name] = {"time_to_tol_s": el, "status": inf.status, "iters": inf.iters, "outer": inf.outer_iters,
+                     "relres_true": inf.relres_true,
+                     "per_class": {k: {"launches": c["launches"], "ms": round(c["ms"], 3),
+                                       "gbs": c["bytes"] / (c["ms"] / 1e3) / 1e9 if c["ms"] > 0 else None,
+                                       "hbm_frac": c["bytes"] / (c["ms"] / 1e3) / 1e9 / hbm_peak if c["ms"] > 0
+                                       else None,
+                                       "tflops": c["flops"] / (c["ms"] / 1e3) / 1e12 if c["ms"] > 0 else None}
+                                   for k, c in prof.items() if c["launches"]}}
+    out["speedup"] = out["fp64"]["time_to_tol_s"] / out["fp32_refine"]["time_to_tol_s"]
+    out["rel_diff_mixed_vs_fp64"] = float(torch.linalg.norm(X["fp32_refine"] - X["fp64"]) / torch.linalg.norm(X["fp64"]))
+    print(json.dumps(out))
+    A.close()
+
+
 def main():
     args = parse_args()
     if args.cpu_sample_worker:
         cpu_sample_worker(args)
+        return
+    if args.config4:
+        config4(args)
         return
     if args.impl == "reference":
         reference_arm(args)

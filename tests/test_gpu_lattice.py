@@ -46,13 +46,31 @@ def rhs(kind, L):
 def test_config3_converges(lat, method, kind):
     kr, L, rp, ci, v, op = lat
     B = rhs(kind, L)
-    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-8, maxit=3000)
+    # for the 12 unit vectors of one site the arithmetic mean of the residuals is a degenerate
+    # economic shadow (see test_point_sources_mean_shadow_breaks_down): use a seeded Gaussian one
+    shadow = None
+    if kind == "point" and method.startswith("egl"):
+        shadow = torch.from_numpy(np.ascontiguousarray(gaussian_block(L.n, 1, seed=5)[:, 0])).cuda()
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-8, maxit=3000, shadow=shadow)
     assert info.status == "OK", info
     assert info.relres_true < 5e-8
     # the true residual recomputed with the oracle's sparse product
     A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
     Xn = X.cpu().numpy()
     assert np.linalg.norm(B - A @ Xn) / np.linalg.norm(B) < 5e-8
+
+
+def test_point_sources_mean_shadow_breaks_down(lat):
+    """With the mean-of-columns shadow (Sec. 5) and one-site point sources, eGl-BiCG breaks down
+    at its second iteration on this lattice: the same in the oracle and on the GPU."""
+    kr, L, rp, ci, v, op = lat
+    B = rhs("point", L)
+    A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
+    ref = oracle.solve("egl_bicg", A, B, tol=1e-8, maxit=10)
+    X, info = kr.kr_solve(op, "egl_bicg", torch.from_numpy(B).cuda(), tol=1e-8, maxit=10)
+    assert ref.status == oracle.Status.BREAKDOWN and info.status == "BREAKDOWN"
+    assert info.iters == ref.iters
+    assert np.allclose(info.history, ref.history, rtol=1e-10, atol=0)
 
 
 @pytest.mark.parametrize("method", ["egl_bicg", "egl_qmr", "bl_bicgstab_rq"])
