@@ -20,7 +20,6 @@ struct RedSpec {
   int kind;        // RedKind
   int ysrc;        // which computed value is Y (linear combination: output index; SpMM: 0)
   int ureg;        // >= 0: U is computed output ureg of this launch; -1: U is read from memory
-  int usrc;        // linear combination: operand index of a memory U (-1: none)
   int gacc;        // accumulator index for RED_GRAM
   const void* U;   // memory operand: n x s block (GRAM, TRACE) or n-vector (SUMV, GRAMV)
   int slot;        // first slot of this reduction in a CTA's partial record
@@ -72,7 +71,7 @@ enum CoefKind : int { COEF_ONE = 0, COEF_SCALAR = 1, COEF_MAT = 2, COEF_DIAG = 3
 
 struct Term {
   int src_kind;        // SrcKind
-  int src_reg;         // SRC_REG: index of an earlier output; SRC_BLOCK / SRC_VEC: operand index
+  int src_reg;         // SRC_REG: index of an earlier output
   const void* src;     // SRC_BLOCK / SRC_VEC pointer
   int coef_kind;       // CoefKind
   int coef_idx;        // COEF_MAT / COEF_DIAG: index into the launch's matrix table
@@ -89,57 +88,30 @@ struct Out {
   Term t[kMaxTerm];
 };
 
-constexpr int kMaxSrc = 10;    // distinct memory operands of one linear-combination launch
-
 struct LinArgs {
   int64_t n;
   int s;
   int nout;
   int nmat;
-  int nsrc;                      // distinct memory operands, all loaded before any store
-  const void* src[kMaxSrc];
-  int src_vec[kMaxSrc];          // n-vector (1) or n x s block (0)
   const double2* mat[kMaxMat];   // device s x s (row-major) or s-vector (diagonal) coefficients
   int mat_is_diag[kMaxMat];
   int mat_neg[kMaxMat];          // stored negated in shared memory
   Out o[kMaxOut];
 };
 
-// Fill the launch's operand table: every memory source of a term and every memory U of a
-// reduction gets an index (equal pointers share one); returns false if there are more than
-// kMaxSrc distinct operands.
+// A reduction whose memory operand U is also written by the same launch is redirected to
+// that output's register: it reduces the updated value (outputs are stored at the end of
+// each row).  Always returns true.
 inline bool resolve_sources(LinArgs& a, RedSet& rs) {
-  a.nsrc = 0;
-  auto add = [&](const void* p, int vec) -> int {
-    for (int i = 0; i < a.nsrc; ++i)
-      if (a.src[i] == p && a.src_vec[i] == vec) return i;
-    if (a.nsrc >= kMaxSrc) return -1;
-    a.src[a.nsrc] = p;
-    a.src_vec[a.nsrc] = vec;
-    return a.nsrc++;
-  };
-  for (int o = 0; o < a.nout; ++o)
-    for (int t = 0; t < a.o[o].nterm; ++t) {
-      Term& tm = a.o[o].t[t];
-      if (tm.src_kind == SRC_REG) continue;
-      tm.src_reg = add(tm.src, tm.src_kind == SRC_VEC ? 1 : 0);
-      if (tm.src_reg < 0) return false;
-    }
   for (int i = 0; i < rs.nred; ++i) {
     RedSpec& r = rs.r[i];
-    r.usrc = -1;
     if (r.ureg >= 0 || r.U == nullptr) continue;
     const int vec = (r.kind == RED_SUMV || r.kind == RED_GRAMV) ? 1 : 0;
     // a U that this launch writes is reduced with its new value (the output's register)
     int written = -1;
     for (int o = 0; o < a.nout; ++o)
       if (a.o[o].dst == r.U && a.o[o].is_vec == vec) written = o;
-    if (written >= 0) {
-      r.ureg = written;
-      continue;
-    }
-    r.usrc = add(r.U, vec);
-    if (r.usrc < 0) return false;
+    if (written >= 0) r.ureg = written;
   }
   return true;
 }

@@ -134,15 +134,6 @@ __device__ __forceinline__ C2<T> pick(const C2<T> (&o)[kMaxOut], int r) {
 }
 
 template <typename T>
-__device__ __forceinline__ C2<T> pick_src(const C2<T> (&x)[kMaxSrc], int r) {
-  C2<T> v = x[0];
-#pragma unroll
-  for (int i = 1; i < kMaxSrc; ++i)
-    if (r == i) v = x[i];
-  return v;
-}
-
-template <typename T>
 __device__ __forceinline__ C2<T> scalar_coef(const double2* p, int conj, int neg) {
   double2 d = *p;
   if (conj) d.y = -d.y;
@@ -171,6 +162,13 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
     ysc = mk<T>((T)a.ay * d.x, (T)a.ay * d.y);
   }
   const T bz = (T)a.bz;
+  // stencil coefficients converted once (a double -> float conversion runs on the FP64 pipe)
+  C2<T> stc = mk<T>((T)a.sc.x, (T)a.sc.y), stm[3], stp[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    stm[q] = mk<T>((T)a.sm[q].x, (T)a.sm[q].y);
+    stp[q] = mk<T>((T)a.sp[q].x, (T)a.sp[q].y);
+  }
   Acc<T, G, NG> acc;
   acc_zero(acc);
   for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
@@ -187,35 +185,24 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
       for (int q = 0; q < 3; ++q) {
         if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
       }
-      C2<T> xs[7];
-      bool hs[7];
-      hs[0] = true;
-      xs[0] = act ? a.V[j * s + c] : czero<T>();
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int qa = 2 - q;  // descending axes for the minus side
-        const bool okm = qa < a.nst && xc[qa] > 0;
-        hs[1 + q] = okm;
-        xs[1 + q] = (act && okm) ? a.V[(j - a.sstr[qa]) * s + c] : czero<T>();
-        const bool okp = q < a.nst && xc[q] < a.sdims[q] - 1;
-        hs[4 + q] = okp;
-        xs[4 + q] = (act && okp) ? a.V[(j + a.sstr[q]) * s + c] : czero<T>();
-      }
       if (act) {
-        y = cmul<T>(mk<T>((T)a.sc.x, (T)a.sc.y), xs[0]);
+        // neighbours one at a time: FMA order centre, -axis d-1..0, +axis 0..d-1
+        y = cmul<T>(stc, a.V[j * s + c]);
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const int qa = 2 - q;
-          if (hs[1 + q]) {
-            if (a.sreal) y = cfmareal<T>((T)a.sm[qa].x, xs[1 + q], y);
-            else y = cfma<T>(mk<T>((T)a.sm[qa].x, (T)a.sm[qa].y), xs[1 + q], y);
+          if (qa < a.nst && xc[qa] > 0) {
+            const C2<T> xv = a.V[(j - a.sstr[qa]) * s + c];
+            if (a.sreal) y = cfmareal<T>(stm[qa].x, xv, y);
+            else y = cfma<T>(stm[qa], xv, y);
           }
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          if (hs[4 + q]) {
-            if (a.sreal) y = cfmareal<T>((T)a.sp[q].x, xs[4 + q], y);
-            else y = cfma<T>(mk<T>((T)a.sp[q].x, (T)a.sp[q].y), xs[4 + q], y);
+          if (q < a.nst && xc[q] < a.sdims[q] - 1) {
+            const C2<T> xv = a.V[(j + a.sstr[q]) * s + c];
+            if (a.sreal) y = cfmareal<T>(stp[q].x, xv, y);
+            else y = cfma<T>(stp[q], xv, y);
           }
         }
         if (scaled) y = cmul<T>(ysc, y);
@@ -341,20 +328,6 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
-    // every memory operand of the row is loaded before any output is stored (outputs may
-    // alias operands, so the compiler could not hoist these loads itself)
-    C2<T> xin[kMaxSrc];
-#pragma unroll
-    for (int q = 0; q < kMaxSrc; ++q) {
-      xin[q] = czero<T>();
-      if (q < a.nsrc) {
-        if (a.src_vec[q]) {
-          if (rowok) xin[q] = reinterpret_cast<const C2<T>*>(a.src[q])[j];
-        } else if (act) {
-          xin[q] = reinterpret_cast<const C2<T>*>(a.src[q])[j * s + c];
-        }
-      }
-    }
     C2<T> o[kMaxOut];
 #pragma unroll
     for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();
@@ -367,7 +340,14 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
         for (int ti = 0; ti < kMaxTerm; ++ti) {
           if (ti < out.nterm) {
             const Term& t = out.t[ti];
-            C2<T> x = (t.src_kind == SRC_REG) ? pick<T>(o, t.src_reg) : pick_src<T>(xin, t.src_reg);
+            C2<T> x = czero<T>();
+            if (t.src_kind == SRC_REG) {
+              x = pick<T>(o, t.src_reg);
+            } else if (t.src_kind == SRC_BLOCK) {
+              if (act) x = reinterpret_cast<const C2<T>*>(t.src)[j * s + c];
+            } else {
+              if (rowok) x = reinterpret_cast<const C2<T>*>(t.src)[j];
+            }
             if (t.xconj) x.y = -x.y;
             if (t.coef_kind == COEF_ONE) {
               if (ti == 0) val = t.neg ? mk<T>(-x.x, -x.y) : x;  // leading copy: no add to zero
@@ -391,13 +371,7 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
             }
           }
         }
-        if (out.is_vec) {
-          o[oi] = rowok ? val : czero<T>();
-          if (out.dst != nullptr && rowok && c == 0) reinterpret_cast<C2<T>*>(out.dst)[j] = val;
-        } else {
-          o[oi] = act ? val : czero<T>();
-          if (out.dst != nullptr && act) reinterpret_cast<C2<T>*>(out.dst)[j * s + c] = val;
-        }
+        o[oi] = (out.is_vec ? rowok : act) ? val : czero<T>();
       }
     }
     if (rs.nred > 0) {
@@ -409,10 +383,24 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
           C2<T> u = czero<T>();
           if (r.ureg >= 0) {
             u = pick<T>(o, r.ureg);
-          } else if (r.usrc >= 0) {
-            u = pick_src<T>(xin, r.usrc);
+          } else if (r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT) {
+            if (act) u = reinterpret_cast<const C2<T>*>(r.U)[j * s + c];
+          } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
+            if (rowok) u = reinterpret_cast<const C2<T>*>(r.U)[j];
           }
           red_add<T, G, NG>(r, ri, acc, y, u, s, grpbase);
+        }
+      }
+    }
+    // outputs are stored only after every operand of the row has been read: an output may
+    // alias an operand, and with no store in between the loads can all be issued up front
+#pragma unroll
+    for (int oi = 0; oi < kMaxOut; ++oi) {
+      if (oi < a.nout && a.o[oi].dst != nullptr) {
+        if (a.o[oi].is_vec) {
+          if (rowok && c == 0) reinterpret_cast<C2<T>*>(a.o[oi].dst)[j] = o[oi];
+        } else if (act) {
+          reinterpret_cast<C2<T>*>(a.o[oi].dst)[j * s + c] = o[oi];
         }
       }
     }
