@@ -173,6 +173,19 @@ KR_API kr_status kr_op_apply_reduce(kr_op op, int32_t adjoint, int32_t s, const 
 KR_API kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
                           void* stream);
 
+/* Complex64 variants of kr_op_apply_reduce and kr_block_reduce: the product and
+ * reduction kernels of the complex64 inner solves of KR_FP32_REFINE, exposed for
+ * testing and for callers that keep their blocks in complex64.  V, Y and U are device
+ * n x s complex64 blocks (interleaved float re, im; U an n-vector for SUMV); the
+ * products and the per-CTA partial sums are formed in FP32, the partial sums are added
+ * in FP64 and out is complex128 (s*s or 1 entries, as above).  kind == 0 in
+ * kr_op_apply_reduce_c64 is a plain product (Y required).  The first complex64 call on
+ * a CSR operator uploads its complex64 copy (kept until kr_op_destroy). */
+KR_API kr_status kr_op_apply_reduce_c64(kr_op op, int32_t adjoint, int32_t s, const float* V, float* Y,
+                                        const float* U, int32_t kind, double* out, void* stream);
+KR_API kr_status kr_block_reduce_c64(int64_t n, int32_t s, const float* U, const float* Y, int32_t kind,
+                                     double* out, void* stream);
+
 /* The reduction of kr_block_reduce without any device allocation by the library,
  * for callers that cannot let a library allocate device memory (an application
  * whose own pool allocator owns all device memory, or a latency-critical loop
@@ -243,6 +256,16 @@ KR_API kr_status kr_profile_enable(int32_t enable, int32_t time_kernels);
 
 /* Copy the counters into *out; reset them when reset != 0. */
 KR_API kr_status kr_profile_read(kr_profile* out, int32_t reset);
+
+/* Kernel choice for complex64 blocks (the inner solves of KR_FP32_REFINE); the paper
+ * has no counterpart.  With enable != 0 (the default), complex64 launches with even s
+ * and no s x s Gram or s x s coefficient matrix run on kernels in which one thread owns
+ * two adjacent columns of a row (16-byte loads and stores); enable == 0 keeps every
+ * launch on the one-column kernels.  Both compute each output entry with the same
+ * operations in the same order; only the grouping of the fused reductions' partial sums
+ * differs.  Process-wide; takes effect for launches issued after the call.  Always
+ * returns KR_OK. */
+KR_API kr_status kr_set_column_pairs(int32_t enable);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 KR_API const char* kr_last_error(void);

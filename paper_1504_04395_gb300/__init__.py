@@ -83,6 +83,8 @@ SIGNATURES = {
     "kr_op_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "kr_op_apply_reduce": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P]),
     "kr_block_reduce": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
+    "kr_op_apply_reduce_c64": (_I32, [_P, _I32, _I32, _P, _P, _P, _I32, _P, _P]),
+    "kr_block_reduce_c64": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
     "kr_thin_qr": (_I32, [_I64, _I32, _P, _P, _P, _P]),
     "kr_solve": (_I32, [_P, _I32, _I32, _P, _P, ctypes.POINTER(KrOptions), _P, ctypes.POINTER(KrInfo)]),
     "kr_adjoint_solve": (_I32, [_P, _I32, _I32, _P, _P, ctypes.POINTER(KrOptions), _P, ctypes.POINTER(KrInfo)]),
@@ -90,6 +92,7 @@ SIGNATURES = {
     "kr_last_error": (ctypes.c_char_p, []),
     "kr_block_reduce_noalloc": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
     "kr_profile_enable": (_I32, [_I32, _I32]),
+    "kr_set_column_pairs": (_I32, [_I32]),
     "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
 }
 
@@ -285,6 +288,37 @@ def kr_block_reduce(U, Y, kind="gram", stream=None):
     return out
 
 
+def kr_op_apply_reduce_c64(op: Operator, V, U=None, kind=0, Y=None, adjoint=False, stream=None, store_y=True):
+    """Complex64 product Y = op(A) V with an optional fused reduction (kind 0: product only).
+
+    V, Y, U: complex64 device tensors; the reduction result is complex128.
+    """
+    torch = _torch()
+    s = V.shape[1]
+    k = RED[kind] if isinstance(kind, str) else int(kind)
+    if Y is None and (store_y or k == 0):
+        Y = torch.empty_like(V)
+    out = torch.empty((s, s) if k == 1 else (1,), dtype=torch.complex128, device=V.device)
+    uptr = ctypes.c_void_p(0) if (U is None) else _dev_ptr(U, "U", torch.complex64)
+    yptr = ctypes.c_void_p(0) if Y is None else _dev_ptr(Y, "Y", torch.complex64, (op.n, s))
+    _check(lib().kr_op_apply_reduce_c64(op.handle, int(adjoint), s, _dev_ptr(V, "V", torch.complex64, (op.n, s)),
+                                        yptr, uptr, k, _dev_ptr(out, "out") if k else ctypes.c_void_p(0),
+                                        _stream(stream)))
+    return Y, (out if k else None)
+
+
+def kr_block_reduce_c64(U, Y, kind="gram", stream=None):
+    """Complex64 block reduction (complex128 result)."""
+    torch = _torch()
+    n, s = Y.shape
+    k = RED[kind] if isinstance(kind, str) else int(kind)
+    out = torch.empty((s, s) if k == 1 else (1,), dtype=torch.complex128, device=Y.device)
+    uptr = ctypes.c_void_p(0) if (U is None) else _dev_ptr(U, "U", torch.complex64)
+    _check(lib().kr_block_reduce_c64(n, s, uptr, _dev_ptr(Y, "Y", torch.complex64), k, _dev_ptr(out, "out"),
+                                     _stream(stream)))
+    return out
+
+
 def kr_block_reduce_noalloc(U, Y, out, kind="gram", stream=None):
     """kr_block_reduce into a caller-provided `out` with no device allocation by the library.
 
@@ -407,6 +441,11 @@ def kr_profile_enable(enable=True, time_kernels=False):
     _check(lib().kr_profile_enable(int(enable), int(time_kernels)))
 
 
+def kr_set_column_pairs(enable=True):
+    """Run complex64 launches with even s on the two-columns-per-thread kernels (default on)."""
+    _check(lib().kr_set_column_pairs(int(bool(enable))))
+
+
 def kr_profile_read(reset=False):
     """Per kernel class: launches, summed CUDA-event ms, algorithmic flops and bytes."""
     p = KrProfile()
@@ -422,5 +461,5 @@ __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
     "kr_op_create_csr", "kr_op_update_values", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
-    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
+    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
 ]

@@ -162,6 +162,11 @@ void kr_options_default(kr_options* opt) {
 
 const char* kr_last_error(void) { return get_error(); }
 
+kr_status kr_set_column_pairs(int32_t enable) {
+  kr::set_pair_kernels(enable != 0);
+  return KR_OK;
+}
+
 kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                            const double* vals, int32_t device, kr_op* out) {
   if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }
@@ -278,21 +283,25 @@ kr_status kr_op_info(kr_op op, int64_t* n, int64_t* nnz, int32_t* real_offdiag) 
   return KR_OK;
 }
 
-static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, const double* U,
-                            int32_t kind, double* out, void* stream) {
+extern "C++" {
+template <typename T>
+static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const T* V, T* Y, const T* U, int32_t kind,
+                            double* out, void* stream) {
   if (!op || !V || bad_s(s)) { set_error("invalid op, V or s"); return KR_BAD_ARG; }
   if (kind && (!out || (kind != KR_RED_NORM2 && !U))) { set_error("reduction needs U and out"); return KR_BAD_ARG; }
   if (kind < 0 || kind > KR_RED_NORM2) { set_error("unknown reduction kind"); return KR_BAD_ARG; }
+  if (!kind && !Y) { set_error("Y is NULL"); return KR_BAD_ARG; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  Workspace& ws = get_workspace(o, s, sizeof(double2), 0, 0, 1);
+  if (sizeof(T) == 4) build_operator_device(o, true);
+  Workspace& ws = get_workspace(o, s, sizeof(C2<T>), 0, 0, 1);
   DevState h{};
   KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
-  SpmmArgs<double> a = op_spmm_args<double>(o, adjoint != 0, s);
-  a.V = reinterpret_cast<const double2*>(V);
-  a.Y = reinterpret_cast<double2*>(Y);
+  SpmmArgs<T> a = op_spmm_args<T>(o, adjoint != 0, s);
+  a.V = reinterpret_cast<const C2<T>*>(V);
+  a.Y = reinterpret_cast<C2<T>*>(Y);
   a.ay = 1.0;
   RedSet rs{};
   rs.partials = ws.partials;
@@ -303,26 +312,33 @@ static kr_status apply_impl(kr_op op, int32_t adjoint, int32_t s, const double* 
     rs.r[0].U = U;
     rs.nslots = kind == KR_RED_GRAM ? s * s : 1;
   }
-  const int grid = row_grid(o.n, s);
-  launch_spmm<double>(a, rs, grid, nullptr, st);
-  if (kind) launch_reduce<double>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
+  const int grid = launch_spmm<T>(a, rs, row_grid(o.n, s), nullptr, st);
+  if (kind) launch_reduce<T>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
   return KR_OK;
   KR_API_END
 }
+}  // extern "C++"
 
 kr_status kr_op_apply(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, void* stream) {
   if (!Y) { set_error("Y is NULL"); return KR_BAD_ARG; }
-  return apply_impl(op, adjoint, s, V, Y, nullptr, 0, nullptr, stream);
+  return apply_impl<double>(op, adjoint, s, V, Y, nullptr, 0, nullptr, stream);
 }
 
 kr_status kr_op_apply_reduce(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, const double* U,
                              int32_t kind, double* out, void* stream) {
   if (kind < KR_RED_GRAM || kind > KR_RED_NORM2) { set_error("unknown reduction kind"); return KR_BAD_ARG; }
-  return apply_impl(op, adjoint, s, V, Y, U, kind, out, stream);
+  return apply_impl<double>(op, adjoint, s, V, Y, U, kind, out, stream);
 }
 
-kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
-                          void* stream) {
+kr_status kr_op_apply_reduce_c64(kr_op op, int32_t adjoint, int32_t s, const float* V, float* Y, const float* U,
+                                 int32_t kind, double* out, void* stream) {
+  return apply_impl<float>(op, adjoint, s, V, Y, U, kind, out, stream);
+}
+
+extern "C++" {
+template <typename T>
+static kr_status block_reduce_impl(int64_t n, int32_t s, const T* U, const T* Y, int32_t kind, double* out,
+                                   void* stream) {
   if (n <= 0 || bad_s(s) || !Y || !out || (kind != KR_RED_NORM2 && !U) || kind < KR_RED_GRAM || kind > KR_RED_NORM2) {
     set_error("invalid arguments");
     return KR_BAD_ARG;
@@ -346,13 +362,23 @@ kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y
   rs.r[0].ureg = -1;
   rs.r[0].U = U;
   rs.nslots = kind == KR_RED_GRAM ? s * s : 1;
-  const int grid = row_grid(n, s);
   const int G = threads_per_row(s);
   if (kind == KR_RED_GRAM && ng_capacity(G) < 1) { set_error("Gram with s > 16 not fused here"); return KR_UNSUPPORTED; }
-  launch_lincomb<double>(a, rs, grid, nullptr, st);
-  launch_reduce<double>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
+  const int grid = launch_lincomb<T>(a, rs, row_grid(n, s), nullptr, st);
+  launch_reduce<T>(ws.partials, grid, rs.nslots, reinterpret_cast<double2*>(out), nullptr, st);
   return KR_OK;
   KR_API_END
+}
+}  // extern "C++"
+
+kr_status kr_block_reduce(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind, double* out,
+                          void* stream) {
+  return block_reduce_impl<double>(n, s, U, Y, kind, out, stream);
+}
+
+kr_status kr_block_reduce_c64(int64_t n, int32_t s, const float* U, const float* Y, int32_t kind, double* out,
+                              void* stream) {
+  return block_reduce_impl<float>(n, s, U, Y, kind, out, stream);
 }
 
 kr_status kr_thin_qr(int64_t n, int32_t s, const double* Z, double* Q, double* S, void* stream) {

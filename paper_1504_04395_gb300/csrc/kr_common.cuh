@@ -46,8 +46,9 @@ template <typename T> __device__ __forceinline__ C2<T> cfmareal(T r, C2<T> b, C2
 }
 template <typename T> __host__ __device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
 template <typename T> __host__ __device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+// a*b with explicit FMAs, so that every kernel rounds a complex product the same way
 template <typename T> __host__ __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+  return mk<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 template <typename T> __host__ __device__ __forceinline__ C2<T> cconj(C2<T> a) { return mk<T>(a.x, -a.y); }
 template <typename T> __host__ __device__ __forceinline__ T cabs2(C2<T> a) { return a.x * a.x + a.y * a.y; }
@@ -72,6 +73,7 @@ template <typename T> __device__ __forceinline__ C2<T> shfl_down(C2<T> v, int d)
 // Number of CTAs used by the grid-stride kernels: a fixed multiple of the SM count so
 // that per-CTA partial sums (and hence every reduction) have a fixed order.
 constexpr int kThreads = 256;
+constexpr int kCtasPerSmRows = 4;  // resident CTAs per SM the row kernels are sized for
 constexpr int kMaxS = 32;
 
 // Reduction kinds of the fused epilogues.

@@ -35,7 +35,7 @@ inline int threads_per_row(int s) {   // G: smallest power of two >= s
   return g;
 }
 inline int ng_capacity(int G) { return G <= 8 ? 2 : (G == 16 ? 1 : 0); }
-constexpr int kCtasPerSm = 4;
+constexpr int kCtasPerSm = kCtasPerSmRows;
 inline int max_row_grid() { return sm_count() * kCtasPerSm; }
 inline int row_grid(int64_t n, int s) {
   const int G = threads_per_row(s);
@@ -46,11 +46,17 @@ inline int row_grid(int64_t n, int s) {
   return (int)(g < cap ? g : cap);
 }
 
+// complex64 row kernels on column pairs (kr_set_column_pairs; on by default)
+bool pair_kernels_enabled();
+void set_pair_kernels(bool on);
+
 // ----- row kernels (kr_rows_f64.cu / kr_rows_f32.cu) -------------------------------------
+// Both return the grid actually launched (the requested grid clamped to the resident CTAs);
+// reductions of the launch's partial records must use that count.
 template <typename T>
-void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
+int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
 template <typename T>
-void launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
+int launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
 template <typename T>
 void launch_reduce(const void* partials, int nparts, int nslots, double2* out, const int* done, cudaStream_t st);
 

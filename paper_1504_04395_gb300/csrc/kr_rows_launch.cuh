@@ -1,9 +1,12 @@
 // Host launchers for the row kernels, instantiated once per element type.
 #pragma once
 
+#include <unordered_map>
+
 #include "kr_internal.h"
 #include "kr_profile.h"
 #include "kr_rows_impl.cuh"
+#include "kr_rows_vec2.cuh"
 
 namespace kr {
 
@@ -17,18 +20,43 @@ static void allow_smem(K kernel, bool& flag) {
   }
 }
 
+// Clamp a grid-stride grid to the CTAs that can be resident at once (at most kCtasPerSm per SM),
+// so that no CTA waits for a second wave.  Depends only on the kernel, its shared memory and the
+// device, so a given launch always gets the same grid (fixed reduction order).
+// The occupancy query is cached per kernel (the caller's cache), device and shared-memory size.
+template <typename K>
+static int resident_grid(K kernel, size_t smem, int grid, std::unordered_map<size_t, int>& cache) {
+  int dev = 0;
+  KR_CUDA(cudaGetDevice(&dev));
+  const size_t key = smem * 256 + (size_t)dev;
+  auto it = cache.find(key);
+  int occ;
+  if (it != cache.end()) {
+    occ = it->second;
+  } else {
+    KR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem));
+    if (occ < 1) occ = 1;
+    if (occ > kCtasPerSm) occ = kCtasPerSm;
+    cache.emplace(key, occ);
+  }
+  const int cap = sm_count() * occ;
+  return grid < cap ? grid : cap;
+}
+
 template <typename T, int G, int NG>
-static void spmm_go(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void spmm_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   static bool attr = false;
   allow_smem(spmm_kernel<T, G, NG>, attr);
   const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>) : 0;
   if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "spmm: too many reduction slots"};
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(spmm_kernel<T, G, NG>, smem, grid, occ);
   spmm_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
   KR_CUDA(cudaGetLastError());
 }
 
 template <typename T, int G>
-static void spmm_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void spmm_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   if (ng == 0) return spmm_go<T, G, 0>(a, rs, grid, done, st);
   if constexpr (NGCap<1, G>::ok) {
     if (ng == 1) return spmm_go<T, G, 1>(a, rs, grid, done, st);
@@ -40,7 +68,7 @@ static void spmm_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int grid, co
 }
 
 template <typename T>
-static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   const int G = threads_per_row(a.s);
   const int ng = count_grams(rs);
   switch (G) {
@@ -54,10 +82,61 @@ static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int grid, cons
   throw CudaError{cudaErrorInvalidValue, "spmm: s out of range"};
 }
 
+// complex64 launches on column pairs (GP threads per row, GP = next power of two >= s/2)
+template <int GP>
+static void spmm2_go(const SpmmArgs<float>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(float2) : 0;
+  if (smem > 48 * 1024) throw CudaError{cudaErrorInvalidValue, "spmm: too many reduction slots"};
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(spmm2_kernel<GP>, smem, grid, occ);
+  spmm2_kernel<GP><<<grid, kThreads, smem, st>>>(a, rs, done);
+  KR_CUDA(cudaGetLastError());
+}
+
+static void spmm2_dispatch(const SpmmArgs<float>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  switch (threads_per_row(a.s / 2)) {
+    case 1: return spmm2_go<1>(a, rs, grid, done, st);
+    case 2: return spmm2_go<2>(a, rs, grid, done, st);
+    case 4: return spmm2_go<4>(a, rs, grid, done, st);
+    case 8: return spmm2_go<8>(a, rs, grid, done, st);
+    case 16: return spmm2_go<16>(a, rs, grid, done, st);
+  }
+  throw CudaError{cudaErrorInvalidValue, "spmm: s out of range"};
+}
+
+template <int GP>
+static void lin2_go(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  size_t smem = (size_t)a.nmat * a.s * sizeof(float2);
+  if (rs.nred > 0) smem += (size_t)(kThreads / 32) * rs.nslots * sizeof(float2);
+  if (smem > 48 * 1024) throw CudaError{cudaErrorInvalidValue, "lincomb: shared memory budget exceeded"};
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(lincomb2_kernel<GP>, smem, grid, occ);
+  lincomb2_kernel<GP><<<grid, kThreads, smem, st>>>(a, rs, done);
+  KR_CUDA(cudaGetLastError());
+}
+
+static void lin2_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  switch (threads_per_row(a.s / 2)) {
+    case 1: return lin2_go<1>(a, rs, grid, done, st);
+    case 2: return lin2_go<2>(a, rs, grid, done, st);
+    case 4: return lin2_go<4>(a, rs, grid, done, st);
+    case 8: return lin2_go<8>(a, rs, grid, done, st);
+    case 16: return lin2_go<16>(a, rs, grid, done, st);
+  }
+  throw CudaError{cudaErrorInvalidValue, "lincomb: s out of range"};
+}
+
 template <typename T>
-void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM, st);
-  spmm_dispatch<T>(a, rs, grid, done, st);
+  bool paired = false;
+  if constexpr (sizeof(T) == 4) {
+    if (pair_kernels_enabled() && pair_ok_spmm(a, rs)) {
+      spmm2_dispatch(a, rs, grid, done, st);
+      paired = true;
+    }
+  }
+  if (!paired) spmm_dispatch<T>(a, rs, grid, done, st);
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s, nnz = (double)a.nnz;
   double f = a.split ? s * (4.0 * nnz + 6.0 * n) : s * 8.0 * nnz;
@@ -72,21 +151,24 @@ void launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* do
   const void* counted[3] = {a.V, a.Y, a.Z};
   b += red_bytes(rs, a.n, a.s, E, counted, 3);
   prof_end(tk, st, f, b);
+  return grid;
 }
 
 template <typename T, int G, int NG>
-static void lin_go(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void lin_go(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   static bool attr = false;
   allow_smem(lincomb_kernel<T, G, NG>, attr);
   size_t smem = (size_t)a.nmat * a.s * a.s * sizeof(C2<T>);
   if (rs.nred > 0) smem += (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>);
   if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "lincomb: shared memory budget exceeded"};
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(lincomb_kernel<T, G, NG>, smem, grid, occ);
   lincomb_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
   KR_CUDA(cudaGetLastError());
 }
 
 template <typename T, int G>
-static void lin_ng(int ng, const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void lin_ng(int ng, const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   if (ng == 0) return lin_go<T, G, 0>(a, rs, grid, done, st);
   if constexpr (NGCap<1, G>::ok) {
     if (ng == 1) return lin_go<T, G, 1>(a, rs, grid, done, st);
@@ -98,15 +180,16 @@ static void lin_ng(int ng, const LinArgs& a, const RedSet& rs, int grid, const i
 }
 
 template <typename T>
-static void lin_dispatch(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
+static void lin_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st);
 
 template <typename T>
-void launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int* done, cudaStream_t st) {
+int launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int* done, cudaStream_t st) {
   LinArgs a = a_in;
   RedSet rs = rs_in;
   if (!resolve_sources(a, rs)) throw CudaError{cudaErrorInvalidValue, "lincomb: too many distinct operands"};
   ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_LINCOMB32 : KC_LINCOMB, st);
-  lin_dispatch<T>(a, rs, grid, done, st);
+  if (sizeof(T) == 4 && pair_kernels_enabled() && pair_ok_lin(a, rs)) lin2_dispatch(a, rs, grid, done, st);
+  else lin_dispatch<T>(a, rs, grid, done, st);
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s;
   double f = 0.0, b = 0.0;
@@ -137,10 +220,11 @@ void launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const in
   f += red_flops(rs, a.n, a.s);
   b += red_bytes(rs, a.n, a.s, E, counted, nc);
   prof_end(tk, st, f, b);
+  return grid;
 }
 
 template <typename T>
-static void lin_dispatch(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
+static void lin_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   const int G = threads_per_row(a.s);
   const int ng = count_grams(rs);
   switch (G) {
@@ -165,8 +249,8 @@ void launch_reduce(const void* partials, int nparts, int nslots, double2* out, c
 }
 
 #define KR_INSTANTIATE_ROWS(T)                                                                               \
-  template void launch_spmm<T>(const SpmmArgs<T>&, const RedSet&, int, const int*, cudaStream_t);           \
-  template void launch_lincomb<T>(const LinArgs&, const RedSet&, int, const int*, cudaStream_t);            \
+  template int launch_spmm<T>(const SpmmArgs<T>&, const RedSet&, int, const int*, cudaStream_t);            \
+  template int launch_lincomb<T>(const LinArgs&, const RedSet&, int, const int*, cudaStream_t);             \
   template void launch_reduce<T>(const void*, int, int, double2*, const int*, cudaStream_t);
 
 }  // namespace kr

@@ -184,6 +184,7 @@ void rebuild_operator_values(Operator& op) {
 
 void build_operator_device(Operator& op, bool want32) {
   if (op.stA.d > 0) return;  // matrix-free: nothing to upload
+  if (op.A.rowptr && (!want32 || op.have32)) return;  // already resident
   const bool split = offdiag_real(op.n, op.h_rowptr, op.h_colidx, op.h_vals);
   op.real_offdiag = split ? 1 : 0;
   HostCsr t = transpose_conj(op.n, op.h_rowptr, op.h_colidx, op.h_vals);
@@ -362,9 +363,9 @@ struct Engine {
     a.ys_conj = ysconj;
     a.ys_neg = ysneg;
     r.rs.partials = ws.partials;
-    const int grid = row_grid(n, sdim);
+    const int grid0 = row_grid(n, sdim);
     if (count_grams(r.rs) <= ng_capacity(threads_per_row(sdim))) {
-      launch_spmm<T>(a, r.rs, grid, done(), st);
+      const int grid = launch_spmm<T>(a, r.rs, grid0, done(), st);
       return reduce(r, grid);
     }
     // register budget exceeded: product stored with the other reductions fused, Grams from memory
@@ -379,7 +380,7 @@ struct Engine {
       map[i] = q.kind == RED_GRAM ? -1 : nong.add(q.kind, q.ysrc, q.ureg, q.U, sdim);
     }
     nong.rs.partials = ws.partials;
-    launch_spmm<T>(a, nong.rs, grid, done(), st);
+    const int grid = launch_spmm<T>(a, nong.rs, grid0, done(), st);
     const int tmp = nong.rs.nred ? reduce(nong, grid) : -1;
     for (int i = 0; i < r.rs.nred; ++i) {
       const RedSpec& q = r.rs.r[i];
@@ -407,10 +408,10 @@ struct Engine {
   // row-local linear combination with fused reductions; returns red offset
   int lin(Lin& L, Reds r = Reds{}) {
     r.rs.partials = ws.partials;
-    const int grid = row_grid(n, L.a.s);
+    const int grid0 = row_grid(n, L.a.s);
     const int G = threads_per_row(L.a.s);
     if (count_grams(r.rs) <= ng_capacity(G)) {
-      launch_lincomb<T>(L.a, r.rs, grid, done(), st);
+      const int grid = launch_lincomb<T>(L.a, r.rs, grid0, done(), st);
       return reduce(r, grid);
     }
     // register budget exceeded: non-Gram reductions fused, each Gram from memory afterwards
@@ -424,7 +425,7 @@ struct Engine {
       map[i] = q.kind == RED_GRAM ? -1 : nong.add(q.kind, q.ysrc, q.ureg, q.U, L.a.s);
     }
     nong.rs.partials = ws.partials;
-    launch_lincomb<T>(L.a, nong.rs, grid, done(), st);
+    const int grid = launch_lincomb<T>(L.a, nong.rs, grid0, done(), st);
     const int tmp = nong.rs.nred ? reduce(nong, grid) : -1;
     for (int i = 0; i < r.rs.nred; ++i) {
       const RedSpec& q = r.rs.r[i];
@@ -445,7 +446,7 @@ struct Engine {
 
   // U^H Y (n x sdim blocks in memory) -> dst (sdim^2 entries), any sdim <= 32
   void gram_from_memory(const void* U, const void* Y, int sdim, double2* dst) {
-    const int grid = row_grid(n, sdim);
+    const int grid0 = row_grid(n, sdim);
     if (ng_capacity(threads_per_row(sdim)) >= 1) {
       Lin g(n, sdim);
       const int go = g.out(nullptr);
@@ -453,7 +454,7 @@ struct Engine {
       Reds gr;
       gr.add(RED_GRAM, go, -1, U, sdim);
       gr.rs.partials = ws.partials;
-      launch_lincomb<T>(g.a, gr.rs, grid, done(), st);
+      const int grid = launch_lincomb<T>(g.a, gr.rs, grid0, done(), st);
       launch_reduce<T>(ws.partials, grid, gr.rs.nslots, dst, done(), st);
       return;
     }
@@ -469,7 +470,7 @@ struct Engine {
       // U column a as a strided vector is not addressable directly: copy it out first
       extract_column(U, sdim, a);
       gr.rs.r[0].U = colbuf();
-      launch_lincomb<T>(g.a, gr.rs, grid, done(), st);
+      const int grid = launch_lincomb<T>(g.a, gr.rs, grid0, done(), st);
       launch_reduce<T>(ws.partials, grid, gr.rs.nslots, dst + (size_t)a * sdim, done(), st);
     }
   }

@@ -1,0 +1,177 @@
+"""Complex64 kernels of the mixed-precision inner solves (GPU).
+
+The block product A V / A^H V and the fused reductions of Algorithms 2-5 in
+complex64, called through kr_op_apply_reduce_c64 and kr_block_reduce_c64, are
+compared with the FP64 oracle evaluated on the complex64 inputs (A, V, U rounded
+to complex64 and widened back, so the only differences are the kernels' FP32
+roundings), with bounds from the standard error analysis of a sum of products.
+
+Both complex64 kernel variants are covered: one column per thread, and two
+adjacent columns per thread (kr_set_column_pairs).  The two compute every output
+entry with the same operations in the same order, so their products are compared
+bit for bit; their reductions group the partial sums differently and agree to FP32
+rounding.
+"""
+import numpy as np
+import pytest
+from scipy.sparse.linalg import splu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from workloads import ConvDiff, convdiff_csr, gaussian_block, random_csr  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+@pytest.fixture(scope="module")
+def kr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as m
+    m.load_library()
+    yield m
+    m.kr_set_column_pairs(True)
+
+
+def c64(x):
+    """Round to complex64 and widen back (the values the complex64 kernels see)."""
+    return np.asarray(x).astype(np.complex64).astype(np.complex128)
+
+
+def dev32(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x).astype(np.complex64))).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def with_pairs(kr, on, fn):
+    kr.kr_set_column_pairs(on)
+    try:
+        return fn()
+    finally:
+        kr.kr_set_column_pairs(True)
+
+
+SIZES = [1, 7, 1000, 5003]
+S_VALUES = [1, 2, 3, 4, 6, 8, 16, 17, 32]
+
+
+@pytest.mark.parametrize("real_offdiag", [False, True])
+@pytest.mark.parametrize("s", S_VALUES)
+def test_c64_spmm_matches_oracle(kr, s, real_offdiag):
+    for n in SIZES:
+        rp, ci, v = random_csr(n, seed=n + s, real_offdiag=real_offdiag)
+        A = oracle.csr_matrix_from_arrays(n, rp, ci, c64(v))
+        op = kr.Operator(n, rp, ci, v)
+        V = c64(gaussian_block(n, s, seed=3))
+        Vd = dev32(V)
+        kmax = int(np.max(np.diff(rp))) if n else 0
+        for adj in (False, True):
+            M = oracle.adjoint(A) if adj else A
+            ref = oracle.spmm(M, V)
+            scale = abs(M) @ np.abs(V)
+            outs = []
+            for pairs in (True, False):
+                Y, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(op, Vd, adjoint=adj))
+                outs.append(Y)
+                # each entry: at most kmax + 1 complex products summed in FP32
+                err = np.abs(host(Y) - ref)
+                assert np.all(err <= 4 * (kmax + 2) * U32 * scale + 1e-30), (n, s, adj, pairs)
+            assert torch.equal(outs[0], outs[1]), (n, s, adj)
+        op.close()
+
+
+@pytest.mark.parametrize("s", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("kind", ["gram", "trace", "sumv", "norm2"])
+def test_c64_fused_reductions(kr, s, kind):
+    if kind == "gram" and s > 16:
+        pytest.skip("a fused s x s Gram is held in registers for s <= 16")
+    n = 6007
+    rp, ci, v = random_csr(n, seed=s)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, c64(v))
+    op = kr.Operator(n, rp, ci, v)
+    V = c64(gaussian_block(n, s, seed=1))
+    U = c64(gaussian_block(n, s, seed=2) if kind != "sumv" else gaussian_block(n, 1, seed=2)[:, 0])
+    Ud = dev32(U) if kind != "norm2" else None
+    res = {}
+    for pairs in (True, False):
+        res[pairs] = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(op, dev32(V), Ud, kind=kind))
+    assert torch.equal(res[True][0], res[False][0])
+    Yk = host(res[True][0])  # the stored complex64 product
+    if kind == "gram":
+        ref = oracle.gram(U, Yk)
+        bound = np.abs(U).T @ np.abs(Yk)
+    elif kind == "trace":
+        ref = np.array([oracle.trace_ip(U, Yk)])
+        bound = np.array([(np.abs(U) * np.abs(Yk)).sum()])
+    elif kind == "sumv":
+        ref = np.array([oracle.sum_ip(U, Yk)])
+        bound = np.array([(np.abs(U)[:, None] * np.abs(Yk)).sum()])
+    else:
+        ref = np.array([np.linalg.norm(Yk) ** 2])
+        bound = ref.copy()
+    for pairs in (True, False):
+        got = host(res[pairs][1]).reshape(ref.shape)
+        if kind == "norm2":
+            got = got.real
+        # FP32 partial sums of at most a few hundred terms per thread, then FP64
+        assert np.all(np.abs(got - ref) <= 1e-4 * bound.reshape(ref.shape)), (kind, pairs)
+    # the stand-alone complex64 reduction of the stored product agrees to FP32 rounding
+    for pairs in (True, False):
+        out2 = with_pairs(kr, pairs, lambda: kr.kr_block_reduce_c64(Ud, res[True][0], kind=kind))
+        got2 = host(out2).reshape(ref.shape)
+        if kind == "norm2":
+            got2 = got2.real
+        assert np.all(np.abs(got2 - ref) <= 1e-4 * bound.reshape(ref.shape)), (kind, pairs)
+    # fixed summation order: bitwise reproducible
+    _, out3 = kr.kr_op_apply_reduce_c64(op, dev32(V), Ud, kind=kind)
+    assert torch.equal(out3, res[True][1])
+    op.close()
+
+
+@pytest.mark.parametrize("dims", [(9, 7, 13), (40, 33, 17)])
+@pytest.mark.parametrize("s", [2, 8, 32])
+def test_c64_stencil_equals_csr(kr, dims, s):
+    """Matrix-free and CSR complex64 products: same entries in the same order, bitwise."""
+    cd = ConvDiff(dims, (0.4, -0.3, 0.2), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    centre, minus, plus = cd.coefficients()
+    st = kr.Operator.stencil(dims, centre, minus, plus)
+    csr = kr.Operator(cd.n, rp, ci, v)
+    Vd = dev32(gaussian_block(cd.n, s, seed=s))
+    for pairs in (True, False):
+        for adj in (False, True):
+            Ys, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(st, Vd, adjoint=adj))
+            Yc, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(csr, Vd, adjoint=adj))
+            assert torch.equal(Ys, Yc), (dims, s, adj, pairs)
+    st.close()
+    csr.close()
+
+
+@pytest.mark.parametrize("method", ["gl_bicg", "egl_bicg", "li_bicg", "gl_bicgstab", "li_bicgstab", "egl_qmr"])
+def test_mixed_solve_with_and_without_pairs(kr, method):
+    """FP64 defect correction over complex64 inner solves converges to the FP64 tolerance on
+    both complex64 kernel variants, to the solution of a direct sparse LU."""
+    cd = ConvDiff((24, 24, 24), (0.6, 0.6, 0.6), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    op = kr.Operator(cd.n, rp, ci, v)
+    s = 8
+    B = gaussian_block(cd.n, s, seed=7)
+    A = oracle.csr_matrix_from_arrays(cd.n, rp, ci, v)
+    X_lu = splu(A.tocsc()).solve(B)  # direct sparse LU: the exact solution to rounding
+    for pairs in (True, False):
+        X, info = with_pairs(kr, pairs, lambda: kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10,
+                                                            maxit=2000, precision=kr.FP32_REFINE))
+        assert info.status == "OK", (method, pairs, info)
+        X = host(X)
+        res = np.linalg.norm(B - A @ X) / np.linalg.norm(B)
+        assert res <= 1.01e-10, (method, pairs, res)
+        assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
+    op.close()
