@@ -104,6 +104,9 @@ typedef struct {
   double relres_true;       /* ||B - A X||_F / ||R_0||_F recomputed in FP64 at exit */
   int32_t status;           /* kr_status of the iteration */
   int32_t outer_iters;      /* KR_FP32_REFINE: defect-correction steps */
+  int32_t fp64_iters;       /* KR_FP32_REFINE: iterations of the FP64 solve that finishes the job when a
+                               complex64 inner solve failed to reduce the FP64 residual (0: none) */
+  int32_t reserved;
 } kr_info;
 
 /* Fill *opt with defaults: tol 1e-8, maxit 500, FP64, default shadow, check_every 8. */

@@ -55,6 +55,8 @@ class KrInfo(ctypes.Structure):
         ("relres_true", ctypes.c_double),
         ("status", ctypes.c_int32),
         ("outer_iters", ctypes.c_int32),
+        ("fp64_iters", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -354,6 +356,7 @@ class SolveInfo:
     relres_true: float
     outer_iters: int
     history: list
+    fp64_iters: int = 0
 
     @property
     def converged(self):
@@ -408,7 +411,8 @@ def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, sh
     nh = (info.outer_iters if precision == FP32_REFINE else info.iters) + 1
     si = SolveInfo(status=STATUS[info.status], iters=info.iters, matvecs=info.matvecs,
                    relres_recursive=info.relres_recursive, relres_true=info.relres_true,
-                   outer_iters=info.outer_iters, history=[hist[i] for i in range(min(nh, maxit + 1))])
+                   outer_iters=info.outer_iters, history=[hist[i] for i in range(min(nh, maxit + 1))],
+                   fp64_iters=info.fp64_iters)
     return X, si
 
 

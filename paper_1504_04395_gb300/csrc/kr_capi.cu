@@ -457,8 +457,8 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   } else {
     // defect correction: R = B - A X in FP64; inner complex64 solve of A D = R; X += D
     build_operator_device(o, true);
-    Workspace& rw = get_workspace(o, s, 24, 3, 0, 1);  // R64, R32, D32 (sized for complex128)
-    void *R64 = rw.blocks[0], *R32 = rw.blocks[1], *D32 = rw.blocks[2];
+    Workspace& rw = get_workspace(o, s, 24, 4, 0, 1);  // R64, R32, D32, X backup (sized for complex128)
+    void *R64 = rw.blocks[0], *R32 = rw.blocks[1], *D32 = rw.blocks[2], *Xkeep = rw.blocks[3];
     const int64_t cnt = o.n * (int64_t)s;
     double res0 = true_residual(o, s, dB, dX, R64, st, adjoint);
     double res = res0;
@@ -467,6 +467,8 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
     inner.shadow_mode = opt.shadow_mode == KR_SHADOW_USER ? KR_SHADOW_DEFAULT : opt.shadow_mode;
     const int max_outer = opt.max_outer > 0 ? opt.max_outer : 30;
     int status = KR_MAXIT, outer = 0;
+    bool fallback = false;
+    inner.stall = 100;
     if (opt.history) opt.history[0] = 1.0;
     if (res0 == 0.0) status = KR_OK;
     else if (!std::isfinite(res0)) status = KR_NAN;
@@ -483,6 +485,7 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
       SolveOut so = run_solve<float>(o, method, s, R32, D32, inner, st, adjoint);
       inf.iters += so.iters;
       inf.matvecs += so.matvecs;
+      KR_CUDA(cudaMemcpyAsync(Xkeep, dX, bytes, cudaMemcpyDeviceToDevice, st));
       {
         ProfToken tk = prof_begin(KC_OTHER, st);
         add_c64_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<double2*>(dX),
@@ -494,11 +497,32 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
       res = true_residual(o, s, dB, dX, R64, st, adjoint);
       ++outer;
       if (opt.history && outer <= opt.maxit) opt.history[outer] = res / res0;
-      if (!std::isfinite(res)) status = KR_NAN;
-      else if (res <= opt.tol * res0) status = KR_OK;
-      else if (res >= prev && (so.status == KR_BREAKDOWN || so.status == KR_NAN || so.iters == 0))
-        status = so.status == KR_NAN ? KR_NAN : KR_BREAKDOWN;
+      if (!std::isfinite(res) || res >= prev) {
+        // the complex64 inner solve did not reduce the FP64 residual (for the block methods the
+        // FP32-accumulated s x s Gram products can make it diverge): restore X, finish in FP64
+        KR_CUDA(cudaMemcpyAsync(dX, Xkeep, bytes, cudaMemcpyDeviceToDevice, st));
+        res = prev;
+        fallback = true;
+        break;
+      }
+      if (res <= opt.tol * res0) status = KR_OK;
       else if (res > 1e8 * res0) status = KR_DIVERGED;
+    }
+    if (fallback && inf.iters < opt.maxit) {
+      // finish in FP64 from the current X, to the caller's tolerance relative to the first residual
+      SolveIn in64 = in;
+      in64.maxit = opt.maxit - inf.iters;
+      in64.tol = res > 0 ? opt.tol * res0 / res : opt.tol;
+      SolveOut so = run_solve<double>(o, method, s, dB, dX, in64, st, adjoint);
+      inf.iters += so.iters;
+      inf.matvecs += so.matvecs;
+      inf.fp64_iters = so.iters;
+      res = true_residual(o, s, dB, dX, R64, st, adjoint);
+      status = res <= opt.tol * res0 ? KR_OK : (so.status == KR_OK ? KR_MAXIT : so.status);
+      if (opt.history && outer + 1 <= opt.maxit) opt.history[outer + 1] = res / res0;
+      ++outer;
+    } else if (fallback) {
+      status = KR_MAXIT;
     }
     inf.outer_iters = outer;
     inf.status = status;

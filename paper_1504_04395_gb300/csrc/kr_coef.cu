@@ -42,10 +42,15 @@ __device__ void monitor(const CoefArgs& a, double rnorm) {
     const double rel = rnorm / st->res0;
     st->rel = rel;
     a.hist[st->iter] = rel;
+    if (rel < st->best) { st->best = rel; st->best_iter = st->iter; }
     if (!isfinite(rel)) { st->status = ST_NAN; st->done = 1; }
     else if (rel <= st->tol) { st->status = ST_OK; st->done = 1; }
     else if (rel > 1e8) { st->status = ST_DIVERGED; st->done = 1; }
     else if (st->iter >= st->maxit) { st->status = ST_MAXIT; st->done = 1; }
+    else if (st->stall > 0 && st->iter - st->best_iter >= max(st->stall, st->best_iter)) {
+      st->status = ST_MAXIT;  // stagnated
+      st->done = 1;
+    }
   }
   __syncthreads();
 }

@@ -33,6 +33,11 @@ struct DevState {
   double2 rot1_c, rot1_s, rot2_c, rot2_s;  // QMR: Givens rotations of the last two steps (c real)
   int have_rot1, have_rot2;
   int pad2[2];
+  // stagnation stop (complex64 inner solves of the defect correction; stall == 0: off):
+  // stop once the residual has not reached a new minimum for max(stall, best_iter) iterations
+  double best;
+  int best_iter;
+  int stall;
 };
 
 // ----- coefficient arena slots (each slot holds up to (2*kMaxS)^2 complex entries) -----

@@ -158,32 +158,58 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
         }
       } else {
         const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
+        // gathers address V as float4 (one column pair) with 32-bit column indices:
+        // row c, pair p is element c * npairs + p (a 32 x 32 -> 64-bit multiply)
+        const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
+        const uint32_t np = (uint32_t)npairs;
+        auto gather = [&](int32_t c) {
+          const float4 v = Vq[(uint64_t)(uint32_t)c * np];
+          Pair q;
+          q.a = make_float2(v.x, v.y);
+          q.b = make_float2(v.z, v.w);
+          return q;
+        };
+        int64_t k = k0;
         if (a.split) {
           const float2 dgv = a.diag[j];
           const Pair xv = ld_pair(a.V, e);
           y.a = cmul<float>(dgv, xv.a);
           y.b = cmul<float>(dgv, xv.b);
-        }
-        // four entries per batch: their indices, values and gathered pairs are all in flight
-        for (int64_t k = k0; k < k1; k += 4) {
-          int32_t col[4];
-          float2 v[4];
-          Pair x[4];
+          // full batches of four entries: indices, values and gathered pairs all in flight
+          for (; k + 4 <= k1; k += 4) {
+            int32_t col[4];
+            float v[4];
+            Pair x[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const bool in = k + u < k1;
-            col[u] = in ? a.colidx[k + u] : 0;
-            if (a.split) v[u] = make_float2(in ? a.offr[k + u] : 0.f, 0.f);
-            else v[u] = in ? a.vals[k + u] : make_float2(0.f, 0.f);
+            for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
           }
+          for (; k < k1; ++k) {
+            const float v = a.offr[k];
+            const Pair x = gather(a.colidx[k]);
+            y.a = cfmareal<float>(v, x.a, y.a);
+            y.b = cfmareal<float>(v, x.b, y.b);
+          }
+        } else {
+          for (; k + 4 <= k1; k += 4) {
+            int32_t col[4];
+            float2 v[4];
+            Pair x[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) x[u] = (k + u < k1) ? ld_pair(a.V, (int64_t)col[u] * s + 2 * p) : pzero();
+            for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (k + u < k1) {
-              if (a.split) { y.a = cfmareal<float>(v[u].x, x[u].a, y.a); y.b = cfmareal<float>(v[u].x, x[u].b, y.b); }
-              else { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
-            }
+            for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
+          }
+          for (; k < k1; ++k) {
+            const float2 v = a.vals[k];
+            const Pair x = gather(a.colidx[k]);
+            y.a = cfma<float>(v, x.a, y.a);
+            y.b = cfma<float>(v, x.b, y.b);
           }
         }
       }

@@ -1281,6 +1281,8 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
   h.s = s;
   h.econ = (method == KRM_EGL_QMR) ? 1 : 0;
   h.status = 4;
+  h.best = HUGE_VAL;
+  h.stall = in.stall;
   KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
   KR_CUDA(cudaMemsetAsync(ws.hist, 0, sizeof(double) * (in.maxit + 1), st));
   DevState* pin = reinterpret_cast<DevState*>(op.pinned);

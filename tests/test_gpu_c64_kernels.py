@@ -174,4 +174,30 @@ def test_mixed_solve_with_and_without_pairs(kr, method):
         res = np.linalg.norm(B - A @ X) / np.linalg.norm(B)
         assert res <= 1.01e-10, (method, pairs, res)
         assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
+        assert info.fp64_iters == 0, (method, pairs, info)
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["bl_bicg_rq", "bl_bicgstab"])
+def test_mixed_block_methods(kr, method):
+    """Block methods under the defect correction.  With its s x s Gram products accumulated in
+    FP32, the complex64 inner Bl-BiCG-rQ solve on this problem stops reducing the residual (an
+    oracle Bl-BiCG run with only its Grams rounded to FP32 diverges the same way); the defect
+    correction then restores X and finishes with the FP64 solver.  Either way the result meets
+    the FP64 tolerance."""
+    cd = ConvDiff((24, 24, 24), (0.6, 0.6, 0.6), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    op = kr.Operator(cd.n, rp, ci, v)
+    B = gaussian_block(cd.n, 8, seed=7)
+    A = oracle.csr_matrix_from_arrays(cd.n, rp, ci, v)
+    X_lu = splu(A.tocsc()).solve(B)
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=3000,
+                          precision=kr.FP32_REFINE)
+    assert info.status == "OK", info
+    if method == "bl_bicg_rq":
+        assert info.fp64_iters > 0, info
+    assert info.iters < 3000
+    X = host(X)
+    assert np.linalg.norm(B - A @ X) / np.linalg.norm(B) <= 1.01e-10
+    assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
     op.close()
