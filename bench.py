@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--operator", choices=("lattice", "csr"), default="lattice",
+                    help="config-4 operator: matrix-free lattice (kr_op_create_lattice4d) or its CSR storage")
     ap.add_argument("--config4", action="store_true",
                     help="mixed precision vs FP64 on the 4D lattice (24^4 x 12, s = 32, eGl-BiCG to 1e-10)")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
@@ -452,7 +454,7 @@ def config4(args):
     row), s = 32 Gaussian right-hand sides, eGl-BiCG (Algorithm 4)."""
     import torch
     from workloads import Lattice4D, gaussian_block, lattice_csr
-    from workloads.lattice import LATTICE_MASS
+    from workloads.lattice import GAMMA, LATTICE_MASS, haar_links
     from paper_1504_04395_gb300 import build
     build.build()
     import paper_1504_04395_gb300 as kr
@@ -460,13 +462,22 @@ def config4(args):
     s = args.s if args.s != 8 else 32
     lat = Lattice4D((L,) * 4, LATTICE_MASS, seed=0)
     t0 = time.perf_counter()
-    rp, ci, v = lattice_csr(lat)
+    links = haar_links(lat.dims, lat.seed)
+    if args.operator == "csr":
+        rp, ci, v = lattice_csr(lat, links)
+        nnz = len(ci)
+    else:
+        nnz = 49 * lat.n
     gen_s = time.perf_counter() - t0
-    A = kr.Operator(lat.n, rp, ci, v)
+    if args.operator == "csr":
+        A = kr.Operator(lat.n, rp, ci, v)
+    else:
+        A = kr.Operator.lattice4d(lat.dims, 4.0 + LATTICE_MASS, -0.5, GAMMA, links)
     B = torch.from_numpy(gaussian_block(lat.n, s, seed=32)).cuda()
     hbm_peak, _ = measured_peaks()
-    out = {"workload": "4D lattice %d^4 x 12 (n=%d, nnz=%d), m=%.2f, s=%d Gaussian RHS, eGl-BiCG to 1e-10"
-                       % (L, lat.n, len(ci), LATTICE_MASS, s), "generation_s": gen_s}
+    out = {"workload": "4D lattice %d^4 x 12 (n=%d, nnz=%d), m=%.2f, s=%d Gaussian RHS, eGl-BiCG to 1e-10, %s operator"
+                       % (L, lat.n, nnz, LATTICE_MASS, s, "matrix-free" if args.operator == "lattice" else "CSR"),
+           "generation_s": gen_s}
     X = {}
     for prec, name in ((kr.FP64, "fp64"), (kr.FP32_REFINE, "fp32_refine")):
         # first call: device copies (complex64 operator for the mixed path) and workspaces

@@ -137,6 +137,24 @@ KR_API kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr,
 KR_API kr_status kr_op_create_stencil(int32_t dim, const int64_t* dims, const double* coeffs, int32_t device,
                                       kr_op* out);
 
+/* Matrix-free 4D lattice operator (Sec. 5, Example 4: a Wilson-type nearest-neighbour
+ * operator, 12 unknowns per site).  Sites x = x_0 + L_0 x_1 + L_0 L_1 x_2 + L_0 L_1 L_2 x_3
+ * on a periodic lattice, unknown (x * 4 + spin) * 3 + colour, and
+ *   (A v)_x = d v_x + hop * sum_mu [ (I - gamma_mu) (x) U_mu(x) v_{x+mu}
+ *                                    + (I + gamma_mu) (x) U_mu(x-mu)^H v_{x-mu} ].
+ * dims[4]: extents L_mu (each >= 3); diag[2]: (re, im) of d; hop: real coefficient;
+ * gamma[4*4*4*2]: the four 4 x 4 matrices gamma_mu, row-major, interleaved (re, im), each
+ * Hermitian with exactly one entry of modulus 1 per row, off the diagonal (a chiral
+ * basis; checked on the host); links[4*sites*9*2]: host array of the 3 x 3 link matrices
+ * U_mu(x), row-major, interleaved, indexed [mu][x].  The caller's arrays are copied.
+ * A product reads the vectors and the links only; each neighbour spinor is projected on
+ * the two independent spin components of (I -+ gamma_mu) before the link multiplies it.
+ * A^H is the same form with gamma_mu -> -gamma_mu and d -> conj(d).  kr_op_info reports
+ * nnz = 49 n (the entries of the equivalent sparse matrix).  kr_grad_values and
+ * kr_op_update_values return KR_UNSUPPORTED. */
+KR_API kr_status kr_op_create_lattice4d(const int64_t* dims, const double* diag, double hop, const double* gamma,
+                                        const double* links, int32_t device, kr_op* out);
+
 /* Replace the stored entries of A (same sparsity pattern, same order as given to
  * kr_op_create_csr): vals[2*nnz] interleaved (re, im), a host pointer
  * (on_device = 0) or a device pointer (on_device != 0).  A^H, the real/complex

@@ -80,6 +80,7 @@ SIGNATURES = {
     "kr_op_create_csr": (_I32, [_I64, _I64, _P, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_destroy": (_I32, [_P]),
     "kr_op_create_stencil": (_I32, [_I32, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "kr_op_create_lattice4d": (_I32, [_P, _P, ctypes.c_double, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_update_values": (_I32, [_P, _P, _I32]),
     "kr_op_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I32)]),
     "kr_op_apply": (_I32, [_P, _I32, _I32, _P, _P, _P]),
@@ -196,6 +197,37 @@ class Operator:
         self.device = int(device)
         h = ctypes.c_void_p()
         _check(lib().kr_op_create_stencil(d, dm.ctypes.data, c.ctypes.data, self.device, ctypes.byref(h)))
+        self._h = h
+        self.nnz = self.info()["nnz"]
+        return self
+
+    @classmethod
+    def lattice4d(cls, dims, diag, hop, gamma, links, device=None):
+        """Matrix-free 4D lattice operator (kr_op_create_lattice4d).
+
+        dims: 4 extents; diag: complex diagonal; hop: real hop coefficient; gamma: (4, 4, 4)
+        complex array of the gamma matrices; links: (4, sites, 3, 3) complex array U_mu(x).
+        """
+        torch = _torch()
+        if device is None:
+            device = torch.cuda.current_device()
+        dm = np.ascontiguousarray(dims, dtype=np.int64)
+        if dm.shape != (4,):
+            raise ValueError("dims must have 4 entries")
+        sites = int(np.prod(dm))
+        g = np.ascontiguousarray(np.asarray(gamma, dtype=np.complex128))
+        if g.shape != (4, 4, 4):
+            raise ValueError("gamma must have shape (4, 4, 4)")
+        U = np.ascontiguousarray(np.asarray(links, dtype=np.complex128))
+        if U.shape != (4, sites, 3, 3):
+            raise ValueError("links must have shape (4, sites, 3, 3)")
+        d = np.array([complex(diag).real, complex(diag).imag], dtype=np.float64)
+        self = cls.__new__(cls)
+        self.n = 12 * sites
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check(lib().kr_op_create_lattice4d(dm.ctypes.data, d.ctypes.data, float(hop), g.ctypes.data, U.ctypes.data,
+                                            self.device, ctypes.byref(h)))
         self._h = h
         self.nnz = self.info()["nnz"]
         return self

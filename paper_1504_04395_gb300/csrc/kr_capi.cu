@@ -250,9 +250,112 @@ kr_status kr_op_create_stencil(int32_t dim, const int64_t* dims, const double* c
   KR_API_END
 }
 
+kr_status kr_op_create_lattice4d(const int64_t* dims, const double* diag, double hop, const double* gamma,
+                                 const double* links, int32_t device, kr_op* out) {
+  if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }
+  *out = nullptr;
+  if (!dims || !diag || !gamma || !links) { set_error("dims, diag, gamma and links must be non-NULL"); return KR_BAD_ARG; }
+  int64_t sites = 1;
+  for (int q = 0; q < 4; ++q) {
+    if (dims[q] < 3) { set_error("every lattice extent must be >= 3"); return KR_BAD_ARG; }
+    sites *= dims[q];
+    if (sites * 12 > 0x7fffffffLL) { set_error("lattice too large"); return KR_BAD_ARG; }
+  }
+  if (!std::isfinite(hop) || !std::isfinite(diag[0]) || !std::isfinite(diag[1])) {
+    set_error("non-finite diagonal or hop coefficient");
+    return KR_BAD_ARG;
+  }
+  // each gamma_mu: one unit-modulus entry per row, off the diagonal, Hermitian
+  int sig[4][4];
+  double2 phi[4][4];
+  for (int mu = 0; mu < 4; ++mu) {
+    for (int r = 0; r < 4; ++r) {
+      int found = -1;
+      for (int col = 0; col < 4; ++col) {
+        const double re = gamma[((mu * 4 + r) * 4 + col) * 2], im = gamma[((mu * 4 + r) * 4 + col) * 2 + 1];
+        if (!std::isfinite(re) || !std::isfinite(im)) { set_error("non-finite gamma entry"); return KR_BAD_ARG; }
+        const double m2 = re * re + im * im;
+        if (m2 == 0.0) continue;
+        if (found >= 0 || std::fabs(m2 - 1.0) > 1e-12) {
+          set_error("gamma matrices must have one entry of modulus 1 per row");
+          return KR_BAD_ARG;
+        }
+        found = col;
+        phi[mu][r] = make_double2(re, im);
+      }
+      if (found < 0 || found == r) { set_error("gamma matrices need one off-diagonal entry per row"); return KR_BAD_ARG; }
+      sig[mu][r] = found;
+    }
+    for (int r = 0; r < 4; ++r) {
+      const int q = sig[mu][r];
+      if (sig[mu][q] != r || std::fabs(phi[mu][q].x - phi[mu][r].x) > 1e-12 ||
+          std::fabs(phi[mu][q].y + phi[mu][r].y) > 1e-12) {
+        set_error("gamma matrices must be Hermitian");
+        return KR_BAD_ARG;
+      }
+    }
+  }
+  const size_t nlink = (size_t)4 * sites * 9;
+  for (size_t i = 0; i < 2 * nlink; ++i)
+    if (!std::isfinite(links[i])) { set_error("non-finite link entry"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { set_error("no CUDA device"); return KR_CUDA_ERROR; }
+  if (device < 0 || device >= ndev) { set_error("device ordinal out of range"); return KR_BAD_ARG; }
+  KR_CUDA(cudaSetDevice(device));
+  auto h = std::make_unique<kr_op_s>();
+  Operator& op = h->op;
+  op.device = device;
+  op.n = 12 * sites;
+  op.nnz = 49 * op.n;  // entries of the equivalent sparse matrix
+  op.real_offdiag = 0;
+  LatticeSpec& L = op.lat;
+  L.on = 1;
+  int64_t stride = 1;
+  for (int q = 0; q < 4; ++q) {
+    L.dims[q] = dims[q];
+    L.str[q] = stride;
+    stride *= dims[q];
+  }
+  L.diag = make_double2(diag[0], diag[1]);
+  L.diagH = make_double2(diag[0], -diag[1]);
+  // projector I + e gamma_mu: e = -1 forward, +1 backward for A; the opposite for A^H
+  auto table = [&](int mu, double e) {
+    LatHop t{};
+    const int r0 = 0, s0 = sig[mu][0];
+    int r1 = 1;
+    while (r1 == r0 || r1 == s0) ++r1;
+    const int reps[2] = {r0, r1};
+    for (int k = 0; k < 2; ++k) {
+      const int r = reps[k], q = sig[mu][r];
+      t.rep[k] = r;
+      t.sig[k] = q;
+      t.pc[k] = make_double2(e * phi[mu][r].x, e * phi[mu][r].y);
+      t.rsrc[r] = k;
+      t.rc[r] = make_double2(1.0, 0.0);
+      t.rsrc[q] = k;
+      t.rc[q] = make_double2(e * phi[mu][q].x, e * phi[mu][q].y);
+    }
+    return t;
+  };
+  for (int mu = 0; mu < 4; ++mu) {
+    L.hops[2 * mu] = table(mu, -1.0);
+    L.hops[2 * mu + 1] = table(mu, +1.0);
+    L.hopsH[2 * mu] = table(mu, +1.0);
+    L.hopsH[2 * mu + 1] = table(mu, -1.0);
+  }
+  L.h_links.assign(links, links + 2 * nlink);
+  for (double& v : L.h_links) v *= hop;
+  build_operator_device(op, false);
+  KR_CUDA(cudaMallocHost(&op.pinned, 4096));
+  *out = h.release();
+  return KR_OK;
+  KR_API_END
+}
+
 kr_status kr_op_update_values(kr_op op, const double* vals, int32_t on_device) {
   if (!op || (!vals && op->op.nnz > 0)) { set_error("op and vals must be non-NULL"); return KR_BAD_ARG; }
-  if (op->op.stA.d > 0) { set_error("stencil operators have no CSR values"); return KR_UNSUPPORTED; }
+  if (op->op.stA.d > 0 || op->op.lat.on) { set_error("matrix-free operators have no CSR values"); return KR_UNSUPPORTED; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
@@ -552,7 +655,7 @@ kr_status kr_adjoint_solve(kr_op op, int32_t method, int32_t s, const double* G,
 
 kr_status kr_grad_values(kr_op op, int32_t s, const double* Lambda, const double* X, double* dvals, void* stream) {
   if (!op || !Lambda || !X || !dvals || bad_s(s)) { set_error("invalid arguments"); return KR_BAD_ARG; }
-  if (op->op.stA.d > 0) { set_error("gradient on the CSR pattern needs a CSR operator"); return KR_UNSUPPORTED; }
+  if (op->op.stA.d > 0 || op->op.lat.on) { set_error("gradient on the CSR pattern needs a CSR operator"); return KR_UNSUPPORTED; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));

@@ -107,8 +107,21 @@ struct StencilSpec {
   double2 c{}, m[3]{}, p[3]{};
 };
 
+// matrix-free 4D lattice operator (kr_op_create_lattice4d)
+struct LatticeSpec {
+  int on = 0;
+  int64_t dims[4] = {1, 1, 1, 1};
+  int64_t str[4] = {0, 0, 0, 0};
+  double2 diag{}, diagH{};     // A and A^H
+  LatHop hops[8], hopsH[8];    // projector tables of A and A^H (gamma -> -gamma)
+  double2* links = nullptr;    // device [4][sites][9], scaled by the hop coefficient
+  float2* links32 = nullptr;   // complex64 copy (mixed precision), built on first use
+  std::vector<double> h_links; // host copy (interleaved re, im), scaled
+};
+
 struct Operator {
   int device = 0;
+  LatticeSpec lat;
   int64_t n = 0, nnz = 0;
   int real_offdiag = 0;
   StencilSpec stA, stAH;     // matrix-free operator (and its adjoint) when stA.d > 0

@@ -33,6 +33,22 @@ struct RedSet {
   RedSpec r[kMaxRed];
 };
 
+// One hop of the 4D lattice operator (direction mu, forward or backward) for one thread's
+// column: the neighbour's spinor psi (4 spins x 3 colours) is projected onto the two spin
+// components h_t = psi[rep_t] + pc_t psi[sig_t] (t = 0, 1), each is multiplied by the
+// link (U for a forward hop, U^H for a backward one: g_t = U h_t), and spin a of the output
+// receives rc_a * g_{rsrc_a}.  For a projector I + e gamma with gamma a phase permutation
+// (gamma[a][sigma a] = phi_a, sigma without fixed points, phi_a phi_{sigma a} = 1) the
+// rank-2 structure gives rep_t / sig_t = an orbit {r, sigma r}, pc_t = e phi_r,
+// rc_r = 1 and rc_{sigma r} = e phi_{sigma r}.
+struct LatHop {
+  int rep[2];
+  int sig[2];
+  int rsrc[4];
+  double2 pc[2];
+  double2 rc[4];
+};
+
 // ---------------------------------------------------------------------------------------
 // SpMM: Y = ay * (A V) + bz * Z  (ay, bz real; optionally ay scaled by a device scalar)
 // ---------------------------------------------------------------------------------------
@@ -61,6 +77,15 @@ struct SpmmArgs {
   int64_t sstr[3];
   double2 sc;                // centre
   double2 sm[3], sp[3];      // minus / plus neighbour along each axis
+  // matrix-free 4D lattice operator (lat = 1 replaces the CSR; rows (site * 4 + spin) * 3 + colour):
+  // y_x = ldiag psi_x + sum_mu [ (I - e gamma_mu) U_mu(x) psi_{x+mu} + (I + e gamma_mu) U_mu(x-mu)^H psi_{x-mu} ]
+  // with the hop coefficient folded into the links and the projector tables in lh
+  int lat;
+  int64_t ldims[4];          // sites per axis (axis 0 fastest), periodic
+  int64_t lstr[4];           // site strides
+  const C2<T>* links;        // [4][sites][3][3] (row-major 3 x 3), scaled by the hop coefficient
+  double2 ldiag;
+  LatHop lh[8];              // hop 2 mu: forward (+mu), hop 2 mu + 1: backward (-mu)
 };
 
 // ---------------------------------------------------------------------------------------

@@ -7,6 +7,7 @@
 #include "kr_profile.h"
 #include "kr_rows_impl.cuh"
 #include "kr_rows_vec2.cuh"
+#include "kr_lattice.cuh"
 
 namespace kr {
 
@@ -82,6 +83,48 @@ static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, con
   throw CudaError{cudaErrorInvalidValue, "spmm: s out of range"};
 }
 
+// matrix-free 4D lattice operator: G threads per (site, colour) unit, 4 rows per thread
+template <typename T, int G, int NG>
+static void lattice_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  static bool attr = false;
+  allow_smem(lattice_kernel<T, G, NG>, attr);
+  const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>) : 0;
+  if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "lattice: too many reduction slots"};
+  const int64_t units_per_cta = (int64_t)(kThreads / 32) * (32 / G);  // (site, colour) units
+  const int64_t tiles = (a.n / 4 + units_per_cta - 1) / units_per_cta;
+  if ((int64_t)grid > tiles) grid = (int)(tiles > 0 ? tiles : 1);
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(lattice_kernel<T, G, NG>, smem, grid, occ);
+  lattice_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
+  KR_CUDA(cudaGetLastError());
+}
+
+template <typename T, int G>
+static void lattice_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  if (ng == 0) return lattice_go<T, G, 0>(a, rs, grid, done, st);
+  if constexpr (NGCap<1, G>::ok) {
+    if (ng == 1) return lattice_go<T, G, 1>(a, rs, grid, done, st);
+  }
+  if constexpr (NGCap<2, G>::ok) {
+    if (ng == 2) return lattice_go<T, G, 2>(a, rs, grid, done, st);
+  }
+  throw CudaError{cudaErrorInvalidValue, "lattice: fused Gram count exceeds the register budget"};
+}
+
+template <typename T>
+static void lattice_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
+  const int ng = count_grams(rs);
+  switch (threads_per_row(a.s)) {
+    case 1: return lattice_ng<T, 1>(ng, a, rs, grid, done, st);
+    case 2: return lattice_ng<T, 2>(ng, a, rs, grid, done, st);
+    case 4: return lattice_ng<T, 4>(ng, a, rs, grid, done, st);
+    case 8: return lattice_ng<T, 8>(ng, a, rs, grid, done, st);
+    case 16: return lattice_ng<T, 16>(ng, a, rs, grid, done, st);
+    case 32: return lattice_ng<T, 32>(ng, a, rs, grid, done, st);
+  }
+  throw CudaError{cudaErrorInvalidValue, "lattice: s out of range"};
+}
+
 // complex64 launches on column pairs (GP threads per row, GP = next power of two >= s/2)
 template <int GP>
 static void spmm2_go(const SpmmArgs<float>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
@@ -129,21 +172,29 @@ static void lin2_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const i
 template <typename T>
 int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM, st);
-  bool paired = false;
+  bool done_launch = false;
+  if (a.lat) {
+    lattice_dispatch<T>(a, rs, grid, done, st);
+    done_launch = true;
+  }
   if constexpr (sizeof(T) == 4) {
-    if (pair_kernels_enabled() && pair_ok_spmm(a, rs)) {
+    if (!done_launch && pair_kernels_enabled() && pair_ok_spmm(a, rs)) {
       spmm2_dispatch(a, rs, grid, done, st);
-      paired = true;
+      done_launch = true;
     }
   }
-  if (!paired) spmm_dispatch<T>(a, rs, grid, done, st);
+  if (!done_launch) spmm_dispatch<T>(a, rs, grid, done, st);
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s, nnz = (double)a.nnz;
   double f = a.split ? s * (4.0 * nnz + 6.0 * n) : s * 8.0 * nnz;
+  // per site and column: diagonal (12 complex products) + 3 colour units x 8 hops x (6 projection
+  // + 6 link + 4 reconstruction complex multiply-adds)
+  if (a.lat) f = s * (n / 12.0) * (6.0 * 12 + 3.0 * 8 * (6 + 6 + 4) * 8);
   if (a.ys != nullptr || a.ay != 1.0) f += 6.0 * s * n;
   if (a.Z != nullptr) f += 4.0 * s * n;
   f += red_flops(rs, a.n, a.s);
   double b = a.nst > 0 ? 0.0 : 8.0 * (n + 1) + 4.0 * nnz + (a.split ? sizeof(T) * nnz + E * n : E * nnz);
+  if (a.lat) b = 4.0 * (n / 12.0) * 9.0 * E;  // the links
   if (a.nst > 0 && !a.sreal) f = s * 8.0 * (nnz + n);
   b += E * n * s;
   if (a.Y != nullptr) b += E * n * s;

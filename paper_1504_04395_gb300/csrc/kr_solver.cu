@@ -38,6 +38,7 @@ Operator::~Operator() {
   ws.clear();
   A.free_all(); AH.free_all(); A32.free_all(); AH32.free_all();
   cudaFree(orig_rowptr); cudaFree(orig_colidx);
+  cudaFree(lat.links); cudaFree(lat.links32);
   if (pinned) cudaFreeHost(pinned);
   cudaSetDevice(prev);
 }
@@ -59,6 +60,20 @@ SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s) {
   a.n = op.n;
   a.s = s;
   a.ay = 1.0;
+  if (op.lat.on) {
+    const LatticeSpec& L = op.lat;
+    a.lat = 1;
+    for (int q = 0; q < 4; ++q) {
+      a.ldims[q] = L.dims[q];
+      a.lstr[q] = L.str[q];
+    }
+    if constexpr (sizeof(T) == 8) a.links = reinterpret_cast<const C2<T>*>(L.links);
+    else a.links = reinterpret_cast<const C2<T>*>(L.links32);
+    a.ldiag = adjoint ? L.diagH : L.diag;
+    for (int h = 0; h < 8; ++h) a.lh[h] = adjoint ? L.hopsH[h] : L.hops[h];
+    a.nnz = op.nnz;
+    return a;
+  }
   if (op.stA.d > 0) {
     const StencilSpec& st = adjoint ? op.stAH : op.stA;
     a.nst = st.d;
@@ -183,6 +198,21 @@ void rebuild_operator_values(Operator& op) {
 }
 
 void build_operator_device(Operator& op, bool want32) {
+  if (op.lat.on) {  // matrix-free lattice: the links (and their complex64 copy)
+    LatticeSpec& L = op.lat;
+    const size_t cnt = L.h_links.size() / 2;
+    if (!L.links) {
+      KR_CUDA(cudaMalloc(&L.links, sizeof(double2) * cnt));
+      KR_CUDA(cudaMemcpy(L.links, L.h_links.data(), sizeof(double2) * cnt, cudaMemcpyHostToDevice));
+    }
+    if (want32 && !L.links32) {
+      std::vector<float2> h32(cnt);
+      for (size_t i = 0; i < cnt; ++i) h32[i] = make_float2((float)L.h_links[2 * i], (float)L.h_links[2 * i + 1]);
+      KR_CUDA(cudaMalloc(&L.links32, sizeof(float2) * cnt));
+      KR_CUDA(cudaMemcpy(L.links32, h32.data(), sizeof(float2) * cnt, cudaMemcpyHostToDevice));
+    }
+    return;
+  }
   if (op.stA.d > 0) return;  // matrix-free: nothing to upload
   if (op.A.rowptr && (!want32 || op.have32)) return;  // already resident
   const bool split = offdiag_real(op.n, op.h_rowptr, op.h_colidx, op.h_vals);

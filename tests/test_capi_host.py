@@ -121,6 +121,47 @@ def test_csr_validation_on_host(libpath):
     assert st == 6
 
 
+def test_lattice_operator_validation_on_host(libpath):
+    """kr_op_create_lattice4d checks extents, coefficients and the gamma matrices on the host,
+    before any device work (no GPU needed)."""
+    import paper_1504_04395_gb300 as kr
+    from workloads.lattice import GAMMA
+    lib = kr.load_library(libpath)
+
+    def create(dims, gamma, diag=(2.2, 0.0), hop=-0.5, links=None):
+        dm = np.ascontiguousarray(dims, dtype=np.int64)
+        sites = int(np.prod(dm))
+        U = np.zeros((4, sites, 3, 3), dtype=np.complex128) if links is None else links
+        U = np.ascontiguousarray(U)
+        g = np.ascontiguousarray(np.asarray(gamma, dtype=np.complex128))
+        d = np.array(diag, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = lib.kr_op_create_lattice4d(dm.ctypes.data, d.ctypes.data, float(hop), g.ctypes.data, U.ctypes.data, 0,
+                                        ctypes.byref(h))
+        return st, h
+
+    st, h = create((3, 3, 2, 3), GAMMA)  # extent below 3
+    assert st == 6 and not h.value and b"extent" in lib.kr_last_error()
+    bad = GAMMA.copy()
+    bad[1, 0, 1] = 0.5  # a second entry in a row
+    st, _ = create((3, 3, 3, 3), bad)
+    assert st == 6 and b"gamma" in lib.kr_last_error()
+    bad = GAMMA.copy()
+    bad[2] = np.diag([1, -1, 1, -1])  # entries on the diagonal
+    st, _ = create((3, 3, 3, 3), bad)
+    assert st == 6 and b"off-diagonal" in lib.kr_last_error()
+    bad = GAMMA.copy()
+    bad[0, 0, 3] = -bad[0, 0, 3]  # gamma[3][0] no longer the conjugate of gamma[0][3]
+    st, _ = create((3, 3, 3, 3), bad)
+    assert st == 6 and b"Hermitian" in lib.kr_last_error()
+    st, _ = create((3, 3, 3, 3), GAMMA, hop=float("nan"))
+    assert st == 6
+    links = np.zeros((4, 81, 3, 3), dtype=np.complex128)
+    links[1, 5, 2, 2] = np.inf
+    st, _ = create((3, 3, 3, 3), GAMMA, links=links)
+    assert st == 6 and b"link" in lib.kr_last_error()
+
+
 def test_solve_argument_checks(libpath):
     import paper_1504_04395_gb300 as kr
     lib = kr.load_library(libpath)
