@@ -318,13 +318,13 @@ def gpu_arm(args):
                           "gbs": c["bytes"] / (c["ms"] / 1000.0) / 1e9 if c["ms"] > 0 else None}
                       for k, c in prof.items()},
     }
-    # DRAM traffic per launch from the committed ncu capture, only while the kernel sources
-    # are the ones that capture measured (otherwise null)
+    # DRAM traffic per launch from the committed ncu capture, only while the files that define
+    # the kernel and its launch are the ones that capture measured (otherwise null)
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
         key = "%s_%d_%d" % (dom, args.grid, s)
-        if key in tr and tr.get("source_digest") == build.source_digest():
+        if key in tr and tr[key].get("kernel_digest") == build.kernel_digest(tr[key]["kernel_sources"]):
             roofline["traffic"] = tr[key]["bytes_per_launch"]
             roofline["traffic_instance"] = tr[key]["instance"]
             roofline["traffic_algorithmic_bytes"] = tr[key]["algorithmic_bytes_per_launch"]

@@ -288,6 +288,14 @@ KR_API kr_status kr_profile_read(kr_profile* out, int32_t reset);
  * returns KR_OK. */
 KR_API kr_status kr_set_column_pairs(int32_t enable);
 
+/* Kernel choice for the matrix-free lattice product (kr_op_create_lattice4d); the paper
+ * has no counterpart.  rows = 4: a thread forms the 4 rows of one (site, colour) pair of
+ * one column (fewer registers, the spin projection repeated per colour); rows = 12: a
+ * thread forms all 12 rows of a site (a quarter fewer flops, a third of the gathers, more
+ * registers); rows = 0 (the default): 12, measured faster in both precisions.
+ * Process-wide; returns KR_BAD_ARG for other values. */
+KR_API kr_status kr_set_lattice_rows_per_thread(int32_t rows);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 KR_API const char* kr_last_error(void);
 

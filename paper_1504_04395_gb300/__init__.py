@@ -96,6 +96,7 @@ SIGNATURES = {
     "kr_block_reduce_noalloc": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
     "kr_profile_enable": (_I32, [_I32, _I32]),
     "kr_set_column_pairs": (_I32, [_I32]),
+    "kr_set_lattice_rows_per_thread": (_I32, [_I32]),
     "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
 }
 
@@ -482,6 +483,11 @@ def kr_set_column_pairs(enable=True):
     _check(lib().kr_set_column_pairs(int(bool(enable))))
 
 
+def kr_set_lattice_rows_per_thread(rows=0):
+    """Matrix-free lattice kernel: 4 rows per thread, 12 (whole sites) or 0 (default per precision)."""
+    _check(lib().kr_set_lattice_rows_per_thread(int(rows)))
+
+
 def kr_profile_read(reset=False):
     """Per kernel class: launches, summed CUDA-event ms, algorithmic flops and bytes."""
     p = KrProfile()
@@ -497,5 +503,5 @@ __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
     "kr_op_create_csr", "kr_op_update_values", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
-    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
+    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_set_lattice_rows_per_thread", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
 ]

@@ -52,6 +52,18 @@ def source_digest() -> str:
     return h.hexdigest()
 
 
+def kernel_digest(files) -> str:
+    """Hash of the named files under csrc/ and the compile flags (the sources that define one
+    kernel and its launch configuration)."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS).encode())
+    return h.hexdigest()
+
+
 def _digest() -> str:
     return hashlib.sha256((source_digest() + platform.machine()).encode()).hexdigest()
 

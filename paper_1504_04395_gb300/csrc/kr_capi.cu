@@ -162,6 +162,12 @@ void kr_options_default(kr_options* opt) {
 
 const char* kr_last_error(void) { return get_error(); }
 
+kr_status kr_set_lattice_rows_per_thread(int32_t rows) {
+  if (rows != 0 && rows != 4 && rows != 12) { set_error("rows must be 0, 4 or 12"); return KR_BAD_ARG; }
+  kr::set_lattice_rows_per_thread(rows);
+  return KR_OK;
+}
+
 kr_status kr_set_column_pairs(int32_t enable) {
   kr::set_pair_kernels(enable != 0);
   return KR_OK;

@@ -47,8 +47,8 @@ __device__ void monitor(const CoefArgs& a, double rnorm) {
     else if (rel <= st->tol) { st->status = ST_OK; st->done = 1; }
     else if (rel > 1e8) { st->status = ST_DIVERGED; st->done = 1; }
     else if (st->iter >= st->maxit) { st->status = ST_MAXIT; st->done = 1; }
-    else if (st->stall > 0 && st->iter - st->best_iter >= max(st->stall, st->best_iter)) {
-      st->status = ST_MAXIT;  // stagnated
+    else if (st->stall > 0 && rel > 1.0 && st->iter - st->best_iter >= max(st->stall, st->best_iter)) {
+      st->status = ST_MAXIT;  // above the starting residual and no new minimum for a while
       st->done = 1;
     }
   }

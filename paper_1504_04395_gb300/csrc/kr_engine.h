@@ -33,8 +33,9 @@ struct DevState {
   double2 rot1_c, rot1_s, rot2_c, rot2_s;  // QMR: Givens rotations of the last two steps (c real)
   int have_rot1, have_rot2;
   int pad2[2];
-  // stagnation stop (complex64 inner solves of the defect correction; stall == 0: off):
-  // stop once the residual has not reached a new minimum for max(stall, best_iter) iterations
+  // stagnation stop (complex64 inner solves of the defect correction; stall == 0: off): stop
+  // once the residual is above its starting norm and has not reached a new minimum for
+  // max(stall, best_iter) iterations
   double best;
   int best_iter;
   int stall;

@@ -49,6 +49,9 @@ inline int row_grid(int64_t n, int s) {
 // complex64 row kernels on column pairs (kr_set_column_pairs; on by default)
 bool pair_kernels_enabled();
 void set_pair_kernels(bool on);
+// rows per thread of the matrix-free lattice product (4: (site, colour) units, 12: whole sites)
+int lattice_rows_per_thread(size_t real_bytes);
+void set_lattice_rows_per_thread(int rows);
 
 // ----- row kernels (kr_rows_f64.cu / kr_rows_f32.cu) -------------------------------------
 // Both return the grid actually launched (the requested grid clamped to the resident CTAs);

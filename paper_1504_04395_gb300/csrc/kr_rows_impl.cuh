@@ -8,7 +8,7 @@ namespace kr {
 // Gram accumulators per thread: NG s x s Grams (column c = this thread's column, G rows of it).
 template <typename T, int G, int NG>
 struct Acc {
-  C2<T> g0[G];                   // first fused Gram
+  C2<T> g0[NG >= 1 ? G : 1];     // first fused Gram
   C2<T> g1[NG >= 2 ? G : 1];     // second fused Gram
   C2<T> v[kMaxRed];
 };
@@ -21,7 +21,7 @@ struct NGCap {  // register budget: at most 16 Gram accumulators per thread
 template <typename T, int G, int NG>
 __device__ __forceinline__ void acc_zero(Acc<T, G, NG>& a) {
 #pragma unroll
-  for (int i = 0; i < G; ++i) a.g0[i] = czero<T>();
+  for (int i = 0; i < (NG >= 1 ? G : 1); ++i) a.g0[i] = czero<T>();
 #pragma unroll
   for (int i = 0; i < (NG >= 2 ? G : 1); ++i) a.g1[i] = czero<T>();
 #pragma unroll

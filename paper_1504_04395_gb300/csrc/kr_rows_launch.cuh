@@ -86,16 +86,27 @@ static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, con
 // matrix-free 4D lattice operator: G threads per (site, colour) unit, 4 rows per thread
 template <typename T, int G, int NG>
 static void lattice_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
-  static bool attr = false;
-  allow_smem(lattice_kernel<T, G, NG>, attr);
   const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>) : 0;
   if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "lattice: too many reduction slots"};
-  const int64_t units_per_cta = (int64_t)(kThreads / 32) * (32 / G);  // (site, colour) units
-  const int64_t tiles = (a.n / 4 + units_per_cta - 1) / units_per_cta;
+  const bool whole_site = lattice_rows_per_thread(sizeof(T)) == 12;
+  // work units: (site, colour) with 4 rows each, or whole sites with 12 rows each
+  const int64_t per_cta = (int64_t)(kThreads / 32) * (32 / G);
+  const int64_t units = whole_site ? a.n / 12 : a.n / 4;
+  const int64_t tiles = (units + per_cta - 1) / per_cta;
   if ((int64_t)grid > tiles) grid = (int)(tiles > 0 ? tiles : 1);
-  thread_local std::unordered_map<size_t, int> occ;
-  grid = resident_grid(lattice_kernel<T, G, NG>, smem, grid, occ);
-  lattice_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
+  if (whole_site) {
+    static bool attr = false;
+    allow_smem(lattice_site_kernel<T, G, NG>, attr);
+    thread_local std::unordered_map<size_t, int> occ;
+    grid = resident_grid(lattice_site_kernel<T, G, NG>, smem, grid, occ);
+    lattice_site_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
+  } else {
+    static bool attr = false;
+    allow_smem(lattice_kernel<T, G, NG>, attr);
+    thread_local std::unordered_map<size_t, int> occ;
+    grid = resident_grid(lattice_kernel<T, G, NG>, smem, grid, occ);
+    lattice_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
+  }
   KR_CUDA(cudaGetLastError());
 }
 
@@ -187,9 +198,13 @@ int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* don
   const double E = sizeof(C2<T>);
   const double n = (double)a.n, s = (double)a.s, nnz = (double)a.nnz;
   double f = a.split ? s * (4.0 * nnz + 6.0 * n) : s * 8.0 * nnz;
-  // per site and column: diagonal (12 complex products) + 3 colour units x 8 hops x (6 projection
-  // + 6 link + 4 reconstruction complex multiply-adds)
-  if (a.lat) f = s * (n / 12.0) * (6.0 * 12 + 3.0 * 8 * (6 + 6 + 4) * 8);
+  // per site and column: diagonal (12 complex products) + 8 hops x (6 projection + 18 link + 12
+  // reconstruction complex multiply-adds) for whole sites; with (site, colour) units the
+  // projection is repeated per colour: 3 x 8 x (6 + 6 + 4)
+  if (a.lat) {
+    if (lattice_rows_per_thread(sizeof(T)) == 12) f = s * (n / 12.0) * (6.0 * 12 + 8 * (6 + 18 + 12) * 8);
+    else f = s * (n / 12.0) * (6.0 * 12 + 3.0 * 8 * (6 + 6 + 4) * 8);
+  }
   if (a.ys != nullptr || a.ay != 1.0) f += 6.0 * s * n;
   if (a.Z != nullptr) f += 4.0 * s * n;
   f += red_flops(rs, a.n, a.s);

@@ -21,7 +21,7 @@ struct SolveIn {
   int shadow_mode = 0;
   const void* shadow = nullptr;
   double time_limit_s = 0.0;
-  int stall = 0;  // > 0: stop after max(stall, best_iter) iterations without a new residual minimum
+  int stall = 0;  // > 0: stop when above the starting residual with no new minimum for max(stall, best_iter) iterations
 };
 
 struct SolveOut {

@@ -30,7 +30,16 @@ def kr():
     build.build()
     import paper_1504_04395_gb300 as m
     m.load_library()
-    return m
+    yield m
+    m.kr_set_lattice_rows_per_thread(0)
+
+
+@pytest.fixture(params=[4, 12], ids=["rows4", "rows12"])
+def variant(kr, request):
+    """Both kernels of the matrix-free product: (site, colour) units and whole sites."""
+    kr.kr_set_lattice_rows_per_thread(request.param)
+    yield request.param
+    kr.kr_set_lattice_rows_per_thread(0)
 
 
 def make(kr, dims, seed=0, links=None):
@@ -51,7 +60,7 @@ def c64(x):
 
 @pytest.mark.parametrize("dims", [(3, 4, 5, 3), (6, 6, 6, 6)])
 @pytest.mark.parametrize("s", [1, 3, 8, 12, 32])
-def test_lattice_product_fp64(kr, dims, s):
+def test_lattice_product_fp64(kr, variant, dims, s):
     L, U, rp, ci, v, op = make(kr, dims)
     assert op.info()["nnz"] == 49 * L.n
     A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
@@ -67,7 +76,7 @@ def test_lattice_product_fp64(kr, dims, s):
 
 
 @pytest.mark.parametrize("s", [1, 2, 8, 32])
-def test_lattice_product_c64(kr, s):
+def test_lattice_product_c64(kr, variant, s):
     dims = (4, 3, 5, 4)
     L, U, rp, ci, v, op = make(kr, dims)
     # the complex64 kernel uses the links rounded to complex64 (times the exact hop -1/2);
@@ -86,7 +95,7 @@ def test_lattice_product_c64(kr, s):
 
 @pytest.mark.parametrize("s", [4, 12])
 @pytest.mark.parametrize("kind", ["gram", "trace", "sumv", "norm2"])
-def test_lattice_fused_reductions(kr, s, kind):
+def test_lattice_fused_reductions(kr, variant, s, kind):
     L, U, rp, ci, v, op = make(kr, (4, 4, 4, 5))
     A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
     V = gaussian_block(L.n, s, seed=1)
@@ -116,7 +125,7 @@ def test_lattice_fused_reductions(kr, s, kind):
 
 
 @pytest.mark.parametrize("method", ["egl_bicg", "bl_bicgstab", "gl_qmr", "bl_bicg_rq"])
-def test_lattice_operator_solves(kr, method):
+def test_lattice_operator_solves(kr, variant, method):
     """Solves with the matrix-free operator reach the tolerance on the oracle's sparse matrix and
     agree with the CSR operator's solution."""
     dims = (6, 6, 6, 6)
