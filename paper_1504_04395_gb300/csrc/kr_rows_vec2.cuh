@@ -27,6 +27,68 @@ __device__ __forceinline__ Pair ld_pair(const float2* base, int64_t idx /* eleme
 __device__ __forceinline__ void st_pair(float2* base, int64_t idx, Pair p) {
   *reinterpret_cast<float4*>(base + idx) = make_float4(p.a.x, p.a.y, p.b.x, p.b.y);
 }
+// Bulk prefetch of bytes [p, p + bytes) into L2 (one instruction for a whole row range;
+// p and bytes multiples of 16, the range inside one allocation)
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Prefetch of bytes [lo, hi) of an allocation of `size` bytes starting at base: the range
+// is widened to 16-byte boundaries but kept inside [0, size rounded down to 16).
+__device__ __forceinline__ void prefetch_l2_range(const void* base, uint64_t lo, uint64_t hi, uint64_t size) {
+  lo &= ~(uint64_t)15;
+  hi = (hi + 15) & ~(uint64_t)15;
+  const uint64_t cap = size & ~(uint64_t)15;
+  if (hi > cap) hi = cap;
+  if (hi > lo) prefetch_l2_bulk(reinterpret_cast<const char*>(base) + lo, (uint32_t)(hi - lo));
+}
+
+// The CSR product's operands for rows [r0, r1) into L2: row pointers, the column indices and
+// values of those rows, the rows of V (the diagonal and nearby gathers), Z and of the
+// reductions' memory operands.  One thread; it reads the two row pointers of the range.
+__device__ __forceinline__ void prefetch_spmm_rows(const SpmmArgs<float>& a, const RedSet& rs, int64_t r0,
+                                                   int64_t r1) {
+  const int64_t n = a.n, s = a.s;
+  prefetch_l2_range(a.rowptr, (uint64_t)r0 * 8, (uint64_t)(r1 + 1) * 8, (uint64_t)(n + 1) * 8);
+  const int64_t k0 = a.rowptr[r0], k1 = a.rowptr[r1];
+  const uint64_t nnz = (uint64_t)a.rowptr[n];
+  prefetch_l2_range(a.colidx, (uint64_t)k0 * 4, (uint64_t)k1 * 4, nnz * 4);
+  if (a.split) {
+    prefetch_l2_range(a.offr, (uint64_t)k0 * 4, (uint64_t)k1 * 4, nnz * 4);
+    prefetch_l2_range(a.diag, (uint64_t)r0 * 8, (uint64_t)r1 * 8, (uint64_t)n * 8);
+  } else {
+    prefetch_l2_range(a.vals, (uint64_t)k0 * 8, (uint64_t)k1 * 8, nnz * 8);
+  }
+  const uint64_t rb = (uint64_t)s * 8, total = (uint64_t)n * rb;
+  prefetch_l2_range(a.V, (uint64_t)r0 * rb, (uint64_t)r1 * rb, total);
+  if (a.Z != nullptr) prefetch_l2_range(a.Z, (uint64_t)r0 * rb, (uint64_t)r1 * rb, total);
+#pragma unroll
+  for (int ri = 0; ri < kMaxRed; ++ri)
+    if (ri < rs.nred && rs.r[ri].U != nullptr && (rs.r[ri].kind == RED_TRACE || rs.r[ri].kind == RED_CDOT))
+      prefetch_l2_range(rs.r[ri].U, (uint64_t)r0 * rb, (uint64_t)r1 * rb, total);
+}
+
+// The rows [r0, r0 + rows) of every block operand of a row-local launch, prefetched into L2
+// by one thread; called kPrefetchAhead grid-stride iterations ahead of the rows' use.
+constexpr int kPrefetchAhead = 2;
+
+__device__ __forceinline__ void prefetch_rows(const LinArgs& a, const RedSet& rs, int64_t r0, int64_t rows) {
+  if (rows <= 0) return;
+  const uint32_t bytes = (uint32_t)(rows * a.s * sizeof(float2));
+#pragma unroll
+  for (int oi = 0; oi < kMaxOut; ++oi)
+    if (oi < a.nout)
+#pragma unroll
+      for (int ti = 0; ti < kMaxTerm; ++ti)
+        if (ti < a.o[oi].nterm && a.o[oi].t[ti].src_kind == SRC_BLOCK)
+          prefetch_l2_bulk(reinterpret_cast<const float2*>(a.o[oi].t[ti].src) + r0 * a.s, bytes);
+#pragma unroll
+  for (int ri = 0; ri < kMaxRed; ++ri)
+    if (ri < rs.nred && rs.r[ri].ureg < 0 && rs.r[ri].U != nullptr &&
+        (rs.r[ri].kind == RED_TRACE || rs.r[ri].kind == RED_CDOT))
+      prefetch_l2_bulk(reinterpret_cast<const float2*>(rs.r[ri].U) + r0 * a.s, bytes);
+}
+
 __device__ __forceinline__ Pair pzero() {
   Pair p;
   p.a = make_float2(0.f, 0.f);
@@ -123,7 +185,21 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
   Acc2 acc;
 #pragma unroll
   for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
-  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
+  const int64_t stride = (int64_t)gridDim.x * rows_per_cta;
+  // CSR with s >= 8: the next rows' matrix entries and operands into L2 (measured: 6-9 % on the
+  // fused product at s = 8-32; at s = 2 the row-pointer reads of the prefetching thread cost more)
+  const bool pf = a.nst == 0 && s >= 8;
+  if (pf && threadIdx.x == 0) {
+    for (int k = 0; k < kPrefetchAhead; ++k) {
+      const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta + k * stride;
+      if (r0 < n) prefetch_spmm_rows(a, rs, r0, r0 + rows_per_cta < n ? r0 + rows_per_cta : n);
+    }
+  }
+  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += stride) {
+    if (pf && threadIdx.x == 0) {
+      const int64_t r0 = base + kPrefetchAhead * stride;
+      if (r0 < n) prefetch_spmm_rows(a, rs, r0, r0 + rows_per_cta < n ? r0 + rows_per_cta : n);
+    }
     const int64_t j = base + warp * RPW + lane / GP;
     const bool rowok = j < n;
     const bool act = rowok && p < npairs;
@@ -276,7 +352,29 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
   Acc2 acc;
 #pragma unroll
   for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
-  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
+  const int64_t stride = (int64_t)gridDim.x * rows_per_cta;
+  // prefetch only for launches streaming 3 or more blocks (measured: a slight loss on a
+  // 2-block reduction, 15 % faster solver updates with 4-6 blocks)
+  int nblk = 0;
+#pragma unroll
+  for (int oi = 0; oi < kMaxOut; ++oi)
+    if (oi < a.nout)
+#pragma unroll
+      for (int ti = 0; ti < kMaxTerm; ++ti)
+        if (ti < a.o[oi].nterm && a.o[oi].t[ti].src_kind == SRC_BLOCK) ++nblk;
+  const bool pf = nblk >= 3;
+  if (pf && threadIdx.x == 0) {
+    // the rows of the first iterations; the loop below keeps kPrefetchAhead iterations ahead
+    for (int k = 0; k < kPrefetchAhead; ++k) {
+      const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta + k * stride;
+      if (r0 < n) prefetch_rows(a, rs, r0, r0 + rows_per_cta < n ? rows_per_cta : n - r0);
+    }
+  }
+  for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += stride) {
+    if (pf && threadIdx.x == 0) {
+      const int64_t r0 = base + kPrefetchAhead * stride;
+      if (r0 < n) prefetch_rows(a, rs, r0, r0 + rows_per_cta < n ? rows_per_cta : n - r0);
+    }
     const int64_t j = base + warp * RPW + lane / GP;
     const bool rowok = j < n;
     const bool act = rowok && p < npairs;
