@@ -378,7 +378,8 @@ def gpu_arm(args):
 
 
 def bench_extras(kr, A, n, s, B, rp, ci, v, args, hbm_peak):
-    """SpMM kernel rates for s in {1, 4, 8, 16} and FP32+refine vs FP64 eGl-BiCG."""
+    """SpMM kernel rates for s in {1, 4, 8, 16} (plain, and fused with a Gram / trace reduction in
+    complex128 and complex64) and FP32+refine vs FP64 eGl-BiCG."""
     import torch
     out = {"spmm": {}}
     nnz = len(ci)
@@ -409,6 +410,36 @@ def bench_extras(kr, A, n, s, B, rp, ci, v, args, hbm_peak):
         out["spmm"][str(ss)] = {"ms": ms, "gbs": byts / ms / 1e6, "hbm_frac": byts / ms / 1e6 / hbm_peak,
                                 "tflops": flops / ms / 1e9, "fp64_frac": flops / ms / 1e9 / FP64_PEAK_TFLOPS}
         del V, Y
+    # fused SpMM + reduction (the product with the s x s Gram U^H (A V) or the trace of it in its
+    # epilogue), complex128 and complex64, rates from the library's launch profile
+    out["spmm_fused"] = {}
+    for ss in (1, 4, 8, 16):
+        for dt, cls, kinds in ((torch.complex128, "spmm", ("gram",)), (torch.complex64, "spmm_c64", ("gram", "trace"))):
+            V = torch.randn(n, ss, dtype=dt, device="cuda")
+            U = torch.randn_like(V)
+            Y = torch.empty_like(V)
+            for kind in kinds:
+                if dt == torch.complex128:
+                    def fn():
+                        kr.kr_op_apply_reduce(A, V, U, kind=kind, Y=Y)
+                else:
+                    def fn():
+                        kr.kr_op_apply_reduce_c64(A, V, U, kind=kind, Y=Y)
+                for _ in range(3):
+                    fn()
+                torch.cuda.synchronize()
+                kr.kr_profile_read(reset=True)
+                kr.kr_profile_enable(True, time_kernels=True)
+                for _ in range(20):
+                    fn()
+                torch.cuda.synchronize()
+                c = kr.kr_profile_read(reset=True)[cls]
+                kr.kr_profile_enable(False)
+                ms = c["ms"] / c["launches"]
+                gbs = c["bytes"] / c["ms"] / 1e6
+                out["spmm_fused"]["%s_%s_s%d" % ("c128" if cls == "spmm" else "c64", kind, ss)] = {
+                    "ms": ms, "gbs": gbs, "hbm_frac": gbs / hbm_peak, "tflops": c["flops"] / c["ms"] / 1e9}
+            del V, U, Y
     # mixed precision: complex64 inner solves (tol 1e-4) in FP64 defect correction, eGl-BiCG to 1e-8
     Bd = torch.from_numpy(B).cuda()
     res = {}

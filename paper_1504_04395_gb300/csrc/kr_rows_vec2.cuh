@@ -353,15 +353,18 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
 #pragma unroll
   for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
   const int64_t stride = (int64_t)gridDim.x * rows_per_cta;
-  // prefetch only for launches streaming 3 or more blocks (measured: a slight loss on a
-  // 2-block reduction, 15 % faster solver updates with 4-6 blocks)
+  // prefetch only for launches streaming 3 or more blocks, read or written (measured: a
+  // slight loss on a 2-block reduction, 15-20 % faster solver updates with 3-6 blocks)
   int nblk = 0;
 #pragma unroll
-  for (int oi = 0; oi < kMaxOut; ++oi)
-    if (oi < a.nout)
+  for (int oi = 0; oi < kMaxOut; ++oi) {
+    if (oi < a.nout) {
+      if (a.o[oi].dst != nullptr) ++nblk;
 #pragma unroll
       for (int ti = 0; ti < kMaxTerm; ++ti)
         if (ti < a.o[oi].nterm && a.o[oi].t[ti].src_kind == SRC_BLOCK) ++nblk;
+    }
+  }
   const bool pf = nblk >= 3;
   if (pf && threadIdx.x == 0) {
     // the rows of the first iterations; the loop below keeps kPrefetchAhead iterations ahead
