@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--operator", choices=("lattice", "csr"), default="lattice",
                     help="config-4 operator: matrix-free lattice (kr_op_create_lattice4d) or its CSR storage")
+    ap.add_argument("--config3", action="store_true",
+                    help="time to 1e-8 per method on the 4D lattice (16^4 x 12, s = 12 point sources and 12 Gaussian)")
     ap.add_argument("--config4", action="store_true",
                     help="mixed precision vs FP64 on the 4D lattice (24^4 x 12, s = 32, eGl-BiCG to 1e-10)")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
@@ -547,10 +549,63 @@ def config4(args):
     A.close()
 
 
+def config3(args):
+    """Time to a relative residual of 1e-8 per method on the 4D lattice operator, 16^4 sites x 12
+    (n = 786,432), s = 12 point sources at one seeded site and s = 12 Gaussian right-hand sides:
+    eGl-BiCG and eGl-QMR (Algorithm 4 and its QMR counterpart) and Bl-BiCGStab-rQ.  For the
+    point sources every method takes a seeded Gaussian shadow (see below)."""
+    import numpy as np
+    import torch
+    from workloads import Lattice4D, gaussian_block, lattice_csr, point_sources
+    from workloads.lattice import GAMMA, LATTICE_MASS, haar_links
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as kr
+    L = args.grid if args.grid != 128 else 16
+    lat = Lattice4D((L,) * 4, LATTICE_MASS, seed=0)
+    links = haar_links(lat.dims, lat.seed)
+    if args.operator == "csr":
+        rp, ci, v = lattice_csr(lat, links)
+        A = kr.Operator(lat.n, rp, ci, v)
+    else:
+        A = kr.Operator.lattice4d(lat.dims, 4.0 + LATTICE_MASS, -0.5, GAMMA, links)
+    site = int(np.random.default_rng(12).integers(0, lat.sites))
+    rhs = {"point": point_sources(lat.n, 12, site), "gauss": gaussian_block(lat.n, 12, seed=12)}
+    # point sources: seeded Gaussian shadows (vector for the economic methods, block for
+    # Bl-BiCGStab-rQ); with the default shadows built from the 12 unit vectors of one site the
+    # first inner products are exact zeros plus rounding noise
+    shadow_vec = torch.from_numpy(np.ascontiguousarray(gaussian_block(lat.n, 1, seed=5)[:, 0])).cuda()
+    shadow_blk = torch.from_numpy(gaussian_block(lat.n, 12, seed=5)).cuda()
+    out = {"workload": "4D lattice %d^4 x 12 (n=%d), m=%.2f, s=12, to 1e-8, %s operator"
+                       % (L, lat.n, LATTICE_MASS, "matrix-free" if args.operator == "lattice" else "CSR"),
+           "results": {}}
+    for kind, B in rhs.items():
+        Bd = torch.from_numpy(B).cuda()
+        for method in ("egl_bicg", "egl_qmr", "bl_bicgstab_rq"):
+            sh = None
+            if kind == "point":
+                sh = shadow_vec if method.startswith("egl") else shadow_blk
+            kr.kr_solve(A, method, Bd, torch.zeros_like(Bd), tol=1e-8, maxit=3, shadow=sh)  # workspaces
+            X = torch.zeros_like(Bd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf = kr.kr_solve(A, method, Bd, X, tol=1e-8, maxit=3000, shadow=sh)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            out["results"]["%s_%s" % (method, kind)] = {
+                "time_to_tol_ms": 1000 * el, "status": inf.status, "iters": inf.iters,
+                "relres_true": inf.relres_true, "rhs_iters_per_s": 12 * inf.iters / el}
+    print(json.dumps(out))
+    A.close()
+
+
 def main():
     args = parse_args()
     if args.cpu_sample_worker:
         cpu_sample_worker(args)
+        return
+    if args.config3:
+        config3(args)
         return
     if args.config4:
         config4(args)
