@@ -38,7 +38,7 @@ from .ops import (
     csr_matrix_from_arrays,
 )
 from .methods import (
-    METHODS, solve, gl_bicg, egl_bicg, bl_bicg, bl_bicg_rq, li_bicg, li_bicgstab,
+    METHODS, solve, gl_bicg, egl_bicg, bl_bicg, bl_bicg_rq, li_bicg, li_bicgstab, li_qmr,
     gl_bicgstab, bl_bicgstab, bl_bicgstab_rq, gl_qmr, egl_qmr, bl_qmr,
 )
 from .scalar import bicg_textbook, bicgstab_textbook
@@ -46,7 +46,7 @@ from .scalar import bicg_textbook, bicgstab_textbook
 __all__ = [
     "Status", "adjoint", "thin_qr", "frob", "trace_ip", "sum_ip", "gram", "spmm",
     "lu_solve", "csr_matrix_from_arrays", "METHODS", "solve",
-    "gl_bicg", "egl_bicg", "bl_bicg", "bl_bicg_rq", "li_bicg", "li_bicgstab",
+    "gl_bicg", "egl_bicg", "bl_bicg", "bl_bicg_rq", "li_bicg", "li_bicgstab", "li_qmr",
     "gl_bicgstab", "bl_bicgstab", "bl_bicgstab_rq", "gl_qmr", "egl_qmr", "bl_qmr",
     "bicg_textbook", "bicgstab_textbook",
 ]

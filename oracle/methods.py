@@ -532,6 +532,103 @@ def _glqmr_core(A, AH, B, X0, Wfirst, mon, w_is_vector):
     return X
 
 
+def li_qmr(A, AH, B, X0, Rh0, mon):
+    """Li-QMR: the loop-interchanged QMR of Sec. 2 (the paper names the Li variants of its three
+    families; Algorithm 1 shows the construction for BiCG).  The s scalar QMR iterations (no
+    look-ahead) on A x_i = b_i with shadow rh_i run in lockstep, one step of every column per
+    iteration; the iteration stops on ||R||_F.  Per column i:
+      v_1 = r_0 / rho_1, w_1 = rh_0 / xi_1, delta_k = w_k^H v_k,
+      alpha_k = w_k^H A v_k / delta_k, beta_k = xi_k delta_k / delta_{k-1},
+      gamma_k = conj(rho_k delta_k / delta_{k-1}),
+      A v_k = v_{k+1} rho_{k+1} + alpha_k v_k + beta_k v_{k-1},
+      A^H w_k = w_{k+1} xi_{k+1} + conj(alpha_k) w_k + gamma_k w_{k-1},
+    the tridiagonal least-squares problem by complex Givens rotations, and
+    d_k = (v_k - u_{k-2,k} d_{k-2} - u_{k-1,k} d_{k-1}) / u_kk, x += tau_k d_k, r -= tau_k A d_k.
+    """
+    s = B.shape[1]
+    X = X0.copy()
+    R = B - spmm(A, X)
+    W = R.copy() if Rh0 is None else Rh0.copy()
+    mon.X = X
+    mon.begin(frob(R))
+    if mon.done:
+        return X
+    rho_k = np.linalg.norm(R, axis=0)
+    xi_k = np.linalg.norm(W, axis=0)
+    if np.any(xi_k == 0) or np.any(rho_k == 0):
+        raise Breakdown("zero column residual or shadow")
+    V = R / rho_k[None, :]
+    W = W / xi_k[None, :]
+    V_prev = np.zeros_like(V)
+    W_prev = np.zeros_like(W)
+
+    def cdot(U, Y):  # column-wise u_i^H y_i
+        return np.einsum("ij,ij->j", U.conj(), Y)
+
+    delta = cdot(W, V)
+    delta_prev = None
+    t = rho_k.astype(np.complex128)
+    rot1 = rot2 = None  # per-column Givens rotations (c, s) of steps k-1 and k-2
+    D1 = np.zeros_like(V)
+    D2 = np.zeros_like(V)
+    AD1 = np.zeros_like(V)
+    AD2 = np.zeros_like(V)
+    k = 0
+    while not mon.done:
+        k += 1
+        if np.any(delta == 0) or not np.all(np.isfinite(delta)):
+            raise Breakdown("Lanczos breakdown: delta_k = 0 in a column")
+        Y = spmm(A, V)
+        Yh = spmm(AH, W)
+        alpha = cdot(W, Y) / delta
+        if k >= 2:
+            beta = xi_k * delta / delta_prev
+            gamma = np.conj(rho_k * delta / delta_prev)
+        else:
+            beta = gamma = np.zeros(s, dtype=np.complex128)
+        Vt = Y - V * alpha[None, :] - V_prev * beta[None, :]
+        Wt = Yh - W * np.conj(alpha)[None, :] - W_prev * gamma[None, :]
+        rho_next = np.linalg.norm(Vt, axis=0)
+        xi_next = np.linalg.norm(Wt, axis=0)
+        u2 = np.zeros(s, dtype=np.complex128)
+        u1 = beta.astype(np.complex128)
+        u0 = alpha.astype(np.complex128)
+        if rot2 is not None:
+            c, sn = rot2
+            u2, u1 = sn * u1, c * u1
+        if rot1 is not None:
+            c, sn = rot1
+            u1, u0 = c * u1 + sn * u0, -np.conj(sn) * u1 + c * u0
+        cs = np.zeros(s)
+        sns = np.zeros(s, dtype=np.complex128)
+        ukk = np.zeros(s, dtype=np.complex128)
+        for i in range(s):
+            cs[i], sns[i], ukk[i] = _givens(u0[i], rho_next[i])
+        if np.any(ukk == 0):
+            raise Breakdown("singular tridiagonal in a column")
+        tau = cs * t
+        t = -np.conj(sns) * t
+        D = (V - D2 * u2[None, :] - D1 * u1[None, :]) / ukk[None, :]
+        AD = (Y - AD2 * u2[None, :] - AD1 * u1[None, :]) / ukk[None, :]
+        X = X + D * tau[None, :]
+        R = R - AD * tau[None, :]
+        mon.matvecs += 2 * s
+        mon.X = X
+        D2, D1 = D1, D
+        AD2, AD1 = AD1, AD
+        rot2, rot1 = rot1, (cs, sns)
+        if mon.step(frob(R)):
+            break
+        if np.any(rho_next == 0) or np.any(xi_next == 0):
+            raise Breakdown("invariant subspace reached in a column")
+        V_prev, W_prev = V, W
+        V = Vt / rho_next[None, :]
+        W = Wt / xi_next[None, :]
+        delta_prev, delta = delta, cdot(W, V)
+        rho_k, xi_k = rho_next, xi_next
+    return X
+
+
 def gl_qmr(A, AH, B, X0, Rh0, mon):
     """Gl-QMR: QMR (no look-ahead) for (I (x) A) x = b with <X, Y> = tr(Y^H X) (Sec. 2)."""
     return _glqmr_core(A, AH, B, X0, Rh0, mon, w_is_vector=False)
@@ -646,6 +743,7 @@ METHODS = {
     "egl_qmr": egl_qmr,
     "li_bicg": li_bicg,
     "li_bicgstab": li_bicgstab,
+    "li_qmr": li_qmr,
 }
 
 

@@ -21,7 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 BICG_LIKE = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "li_bicg"]
 STAB_LIKE = ["bl_bicgstab", "bl_bicgstab_rq", "gl_bicgstab", "li_bicgstab"]
-QMR_LIKE = ["gl_qmr", "egl_qmr", "bl_qmr"]
+QMR_LIKE = ["gl_qmr", "egl_qmr", "bl_qmr", "li_qmr"]
 ALL = BICG_LIKE + STAB_LIKE + QMR_LIKE
 
 
@@ -388,6 +388,31 @@ def test_global_qmr_quasi_minimal(k):
     r = oracle.solve("gl_qmr", A, B, tol=0.0, maxit=k)
     x_bf = _qmr_bruteforce(K, vec(B)[:, None], vec(B)[:, None], k)[:, 0]
     assert rel(vec(r.X), x_bf) < 1e-9
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_li_qmr_is_columnwise_quasi_minimal(k):
+    """Li-QMR (loop interchange, Sec. 2): column i after k steps is the quasi-minimal-residual
+    iterate of the single system A x = b_i with shadow rh_i, built from a dense basis."""
+    A, B = problem(N=6, s=3, shift=0.3j)
+    Rh0 = gaussian_block(B.shape[0], 3, 17)
+    Ad = A.toarray()
+    r = oracle.solve("li_qmr", A, B, tol=0.0, maxit=k, shadow=Rh0)
+    assert r.iters == k
+    for i in range(3):
+        x_bf = _qmr_bruteforce(Ad, B[:, i:i + 1], Rh0[:, i:i + 1], k)[:, 0]
+        assert rel(r.X[:, i], x_bf) < 1e-9, i
+
+
+def test_li_qmr_columns_are_independent():
+    """Loop interchange: a column's iterates do not depend on the other columns (here: the
+    same column solved alone, and the columns in reversed order)."""
+    A, B = problem(N=8, s=3, shift=0.3j)
+    r = oracle.solve("li_qmr", A, B, tol=0.0, maxit=7)
+    alone = oracle.solve("li_qmr", A, B[:, 1:2], tol=0.0, maxit=7)
+    rev = oracle.solve("li_qmr", A, B[:, ::-1].copy(), tol=0.0, maxit=7)
+    assert rel(r.X[:, 1], alone.X[:, 0]) < 1e-13
+    assert rel(r.X[:, ::-1], rev.X) < 1e-13
 
 
 # ------------------------------------------------------------------------------------------
