@@ -67,7 +67,8 @@ typedef enum {
   KR_GL_QMR = 8,          /* Gl-QMR (Sec. 2, global principle) */
   KR_EGL_QMR = 9,         /* eGl-QMR (Sec. 4) */
   KR_LI_BICG = 10,        /* Li-BiCG, Algorithm 1 (Sec. 2) */
-  KR_LI_BICGSTAB = 11     /* Li-BiCGStab: loop interchange (Sec. 2) applied to BiCGStab */
+  KR_LI_BICGSTAB = 11,    /* Li-BiCGStab: loop interchange (Sec. 2) applied to BiCGStab */
+  KR_LI_QMR = 12          /* Li-QMR: loop interchange (Sec. 2) applied to QMR (no look-ahead) */
 } kr_method;
 
 typedef enum {

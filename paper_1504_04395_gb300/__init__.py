@@ -23,7 +23,7 @@ from .build import LIBPATH
 METHODS = {
     "bl_bicg": 0, "bl_bicg_rq": 1, "gl_bicg": 2, "egl_bicg": 3, "bl_bicgstab": 4,
     "bl_bicgstab_rq": 5, "gl_bicgstab": 6, "bl_qmr": 7, "gl_qmr": 8, "egl_qmr": 9, "li_bicg": 10,
-    "li_bicgstab": 11,
+    "li_bicgstab": 11, "li_qmr": 12,
 }
 STATUS = {0: "OK", 1: "BREAKDOWN", 2: "DIVERGED", 3: "NAN", 4: "MAXIT", 5: "TIMEOUT", 6: "BAD_ARG",
           7: "OOM", 8: "CUDA_ERROR", 9: "UNSUPPORTED"}

@@ -15,6 +15,10 @@ using namespace small;
 namespace {
 
 enum : int { ST_OK = 0, ST_BREAKDOWN = 1, ST_DIVERGED = 2, ST_NAN = 3, ST_MAXIT = 4 };
+// fields of the per-column Li-QMR state (slot SL_TMP5, field f of column c at f * s + c)
+enum : int {
+  LQ_RHO = 0, LQ_XI, LQ_T, LQ_DELTA, LQ_DELTAP, LQ_ROT1C, LQ_ROT1S, LQ_ROT2C, LQ_ROT2S, LQ_RHON, LQ_XIN
+};
 
 __device__ __forceinline__ double2* SLP(const CoefArgs& a, int i) { return a.ar + (size_t)i * kSlotElems; }
 
@@ -546,6 +550,124 @@ __global__ void __launch_bounds__(256) coef_kernel(CoefArgs a) {
       monitor(a, sqrt(red[a.i0].x));
       if (is_done(st)) break;
       if (threadIdx.x == 0 && (st->rho_n == 0.0 || st->xi_n == 0.0)) { st->status = ST_BREAKDOWN; st->done = 1; }
+      break;
+    }
+    // ------------------------------------------------------------ Li-QMR (one scalar QMR per column)
+    // per-column state in slot SL_TMP5: field f of column c at [f * s + c]
+    case PH_LQ_INIT: {  // i0 ||r_c||^2, i1 ||w_c||^2 (column-wise)
+      if (threadIdx.x == 0) {
+        double2* Q = SLP(a, SL_TMP5);
+        for (int c = 0; c < s; ++c) {
+          const double rho = sqrt(red[a.i0 + c].x), xi = sqrt(red[a.i1 + c].x);
+          if (!isfinite(rho) || !isfinite(xi)) { st->status = ST_NAN; st->done = 1; break; }
+          if (rho == 0.0 || xi == 0.0) { st->status = ST_BREAKDOWN; st->done = 1; break; }
+          Q[LQ_RHO * s + c] = make_double2(rho, 0.0);
+          Q[LQ_XI * s + c] = make_double2(xi, 0.0);
+          Q[LQ_T * s + c] = make_double2(rho, 0.0);
+          SLP(a, SL_INVRHO)[c] = make_double2(1.0 / rho, 0.0);
+          SLP(a, SL_INVXI)[c] = make_double2(1.0 / xi, 0.0);
+        }
+        st->k = 0;
+        st->have_rot1 = st->have_rot2 = 0;
+      }
+      break;
+    }
+    case PH_LQ_DELTA: {  // i0 w_c^H v_c
+      if (threadIdx.x == 0) {
+        double2* Q = SLP(a, SL_TMP5);
+        for (int c = 0; c < s; ++c) {
+          Q[LQ_DELTA * s + c] = red[a.i0 + c];
+          Q[LQ_DELTAP * s + c] = make_double2(0.0, 0.0);
+        }
+      }
+      break;
+    }
+    case PH_LQ_COEF1: {  // i0 w_c^H (A v_c)
+      if (threadIdx.x == 0) {
+        double2* Q = SLP(a, SL_TMP5);
+        st->k += 1;
+        for (int c = 0; c < s; ++c) {
+          const double2 d = Q[LQ_DELTA * s + c];
+          if (!finite2(d)) { st->status = ST_NAN; st->done = 1; break; }
+          if (d.x == 0.0 && d.y == 0.0) { st->status = ST_BREAKDOWN; st->done = 1; break; }
+          SLP(a, SL_ALPHA)[c] = cdiv(red[a.i0 + c], d);
+          double2 be = make_double2(0.0, 0.0), ga = make_double2(0.0, 0.0);
+          if (st->k >= 2) {
+            const double2 q = cdiv(d, Q[LQ_DELTAP * s + c]);
+            const double xi = Q[LQ_XI * s + c].x, rho = Q[LQ_RHO * s + c].x;
+            be = make_double2(xi * q.x, xi * q.y);
+            ga = cj(make_double2(rho * q.x, rho * q.y));
+          }
+          SLP(a, SL_BETA)[c] = be;
+          SLP(a, SL_GAMMA)[c] = ga;
+        }
+      }
+      break;
+    }
+    case PH_LQ_COEF2: {  // i0 ||vt_c||^2, i1 ||wt_c||^2, i2 wt_c^H vt_c
+      if (threadIdx.x == 0) {
+        double2* Q = SLP(a, SL_TMP5);
+        for (int c = 0; c < s; ++c) {
+          const double rn = sqrt(red[a.i0 + c].x), xn = sqrt(red[a.i1 + c].x);
+          double2 u2 = make_double2(0.0, 0.0), u1 = SLP(a, SL_BETA)[c], u0 = SLP(a, SL_ALPHA)[c];
+          if (st->have_rot2) {
+            const double cr = Q[LQ_ROT2C * s + c].x;
+            const double2 sn = Q[LQ_ROT2S * s + c];
+            u2 = cm(sn, u1);
+            u1 = make_double2(cr * u1.x, cr * u1.y);
+          }
+          if (st->have_rot1) {
+            const double cr = Q[LQ_ROT1C * s + c].x;
+            const double2 sn = Q[LQ_ROT1S * s + c];
+            const double2 n1 = make_double2(cr * u1.x + cm(sn, u0).x, cr * u1.y + cm(sn, u0).y);
+            const double2 n0 = make_double2(-cm(cj(sn), u1).x + cr * u0.x, -cm(cj(sn), u1).y + cr * u0.y);
+            u1 = n1;
+            u0 = n0;
+          }
+          double cr;
+          double2 sn, ukk;
+          givens(u0, make_double2(rn, 0.0), &cr, &sn, &ukk);
+          if (!finite2(ukk) || !isfinite(rn) || !isfinite(xn)) { st->status = ST_NAN; st->done = 1; break; }
+          if (ukk.x == 0.0 && ukk.y == 0.0) { st->status = ST_BREAKDOWN; st->done = 1; break; }
+          const double2 tc = Q[LQ_T * s + c];
+          const double2 tau = make_double2(cr * tc.x, cr * tc.y);
+          Q[LQ_T * s + c] = neg(cm(cj(sn), tc));
+          const double2 iu = cdiv(make_double2(1.0, 0.0), ukk);
+          SLP(a, SL_CV)[c] = iu;
+          SLP(a, SL_CD2)[c] = neg(cm(u2, iu));
+          SLP(a, SL_CD1)[c] = neg(cm(u1, iu));
+          SLP(a, SL_TAU)[c] = tau;
+          SLP(a, SL_NTAU)[c] = neg(tau);
+          Q[LQ_ROT2C * s + c] = Q[LQ_ROT1C * s + c];
+          Q[LQ_ROT2S * s + c] = Q[LQ_ROT1S * s + c];
+          Q[LQ_ROT1C * s + c] = make_double2(cr, 0.0);
+          Q[LQ_ROT1S * s + c] = sn;
+          Q[LQ_RHON * s + c] = make_double2(rn, 0.0);
+          Q[LQ_XIN * s + c] = make_double2(xn, 0.0);
+          SLP(a, SL_INVRHO)[c] = make_double2(rn > 0.0 ? 1.0 / rn : 0.0, 0.0);
+          SLP(a, SL_INVXI)[c] = make_double2(xn > 0.0 ? 1.0 / xn : 0.0, 0.0);
+          const double2 tw = red[a.i2 + c];
+          const double f = (rn > 0.0 && xn > 0.0) ? 1.0 / (rn * xn) : 0.0;
+          Q[LQ_DELTAP * s + c] = Q[LQ_DELTA * s + c];
+          Q[LQ_DELTA * s + c] = make_double2(tw.x * f, tw.y * f);
+          Q[LQ_RHO * s + c] = make_double2(rn, 0.0);
+          Q[LQ_XI * s + c] = make_double2(xn, 0.0);
+        }
+        if (!st->done) {
+          st->have_rot2 = st->have_rot1;
+          st->have_rot1 = 1;
+        }
+      }
+      break;
+    }
+    case PH_LQ_MON: {  // i0 ||R||_F^2
+      monitor(a, sqrt(red[a.i0].x));
+      if (is_done(st)) break;
+      if (threadIdx.x == 0) {
+        const double2* Q = SLP(a, SL_TMP5);
+        for (int c = 0; c < s; ++c)
+          if (Q[LQ_RHON * s + c].x == 0.0 || Q[LQ_XIN * s + c].x == 0.0) { st->status = ST_BREAKDOWN; st->done = 1; break; }
+      }
       break;
     }
     // ------------------------------------------------------------ Bl-QMR

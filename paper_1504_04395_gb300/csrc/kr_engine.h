@@ -61,6 +61,7 @@ enum Phase : int {
   PH_SC_RHO0, PH_SC_ALPHA, PH_SC_BETA,                 // Gl/eGl-BiCG (scalar)
   PH_LI_RHO0, PH_LI_ALPHA, PH_LI_BETA,                 // Li-BiCG (diagonal)
   PH_LS_ALPHA, PH_LS_OMEGA, PH_LS_BETA,                // Li-BiCGStab (diagonal)
+  PH_LQ_INIT, PH_LQ_DELTA, PH_LQ_COEF1, PH_LQ_COEF2, PH_LQ_MON,  // Li-QMR (per column)
   PH_BL_G0, PH_BL_ALPHA, PH_BL_BETA,                   // Bl-BiCG
   PH_QR1, PH_QR2,                                      // CholQR passes
   PH_RQ_INIT, PH_RQ_ALPHA, PH_RQ_C, PH_RQ_BETA,        // Bl-BiCG-rQ

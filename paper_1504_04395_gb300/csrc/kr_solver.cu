@@ -1209,6 +1209,109 @@ void run_gl_qmr(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll, bool
   }
 }
 
+// Li-QMR: s scalar QMR iterations (no look-ahead) in lockstep, the loop interchange of
+// Sec. 2 applied to QMR; every coefficient is a per-column (diagonal) one and every inner
+// product a column-wise one (RED_CDOT).  Stops on ||R||_F.
+template <typename T>
+void run_li_qmr(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
+  Engine<T>& E = c.E;
+  void *R = E.blk(0), *V = E.blk(1), *Vp = E.blk(2), *Y = E.blk(3), *D1 = E.blk(4), *D2 = E.blk(5),
+       *AD1 = E.blk(6), *AD2 = E.blk(7), *W = E.blk(8), *Wp = E.blk(9), *Yh = E.blk(10), *Wstart = E.blk(11);
+  init_residual(E, c.B, c.X, R);
+  make_shadow(E, R, Wstart, c.shadow_mode, c.shadow);
+  int offR, slR, offW, slW;
+  {
+    Lin L(E.n, E.s);
+    const int o = L.out(nullptr);
+    L.blk(o, R);
+    Reds r;
+    slR = r.add(RED_CDOT, o, o, nullptr, E.s);  // ||r_c||^2
+    offR = E.lin(L, r);
+    Lin Lw(E.n, E.s);
+    const int ow = Lw.out(nullptr);
+    Lw.blk(ow, Wstart);
+    Reds rw;
+    slW = rw.add(RED_CDOT, ow, ow, nullptr, E.s);  // ||w_c||^2
+    offW = E.lin(Lw, rw);
+  }
+  E.coef(PH_LQ_INIT, offR + slR, offW + slW);
+  const size_t bytes = (size_t)E.n * E.s * sizeof(C2<T>);
+  KR_CUDA(cudaMemsetAsync(D1, 0, bytes, E.st));
+  KR_CUDA(cudaMemsetAsync(D2, 0, bytes, E.st));
+  KR_CUDA(cudaMemsetAsync(AD1, 0, bytes, E.st));
+  KR_CUDA(cudaMemsetAsync(AD2, 0, bytes, E.st));
+  KR_CUDA(cudaMemsetAsync(Vp, 0, bytes, E.st));
+  KR_CUDA(cudaMemsetAsync(Wp, 0, bytes, E.st));
+  {
+    Lin Lw(E.n, E.s);
+    const int ow = Lw.out(W);
+    Lw.blk(ow, Wstart, dg(E.slot(SL_INVXI)));
+    E.lin(Lw);
+    Lin L(E.n, E.s);
+    const int ov = L.out(V);
+    L.blk(ov, R, dg(E.slot(SL_INVRHO)));
+    Reds r;
+    const int sl = r.add(RED_CDOT, ov, -1, W, E.s);  // w_c^H v_c
+    const int off = E.lin(L, r);
+    E.coef(PH_LQ_DELTA, off + sl);
+  }
+  for (int it = 0; it < maxit; ++it) {
+    E.red_top = 0;
+    Reds r1;
+    const int s1 = r1.add(RED_CDOT, 0, -1, W, E.s);  // w_c^H (A v_c)
+    const int o1 = E.spmm(false, E.s, V, Y, r1);
+    E.spmm(true, E.s, W, Yh);
+    E.coef(PH_LQ_COEF1, o1 + s1);
+    // wt = A^H w - conj(alpha) w - gamma w_prev  (into Wp), column-wise norms
+    Lin Lw(E.n, E.s);
+    const int ow = Lw.out(Wp);
+    Lw.blk(ow, Yh);
+    Lw.blk(ow, W, dg(E.slot(SL_ALPHA), true, true));
+    Lw.blk(ow, Wp, dg(E.slot(SL_GAMMA), false, true));
+    Reds rw;
+    const int sw = rw.add(RED_CDOT, ow, ow, nullptr, E.s);
+    const int offw = E.lin(Lw, rw);
+    // vt = A v - alpha v - beta v_prev  (into Vp), column-wise norms and wt_c^H vt_c
+    Lin Lv(E.n, E.s);
+    const int ov = Lv.out(Vp);
+    Lv.blk(ov, Y);
+    Lv.blk(ov, V, dg(E.slot(SL_ALPHA), false, true));
+    Lv.blk(ov, Vp, dg(E.slot(SL_BETA), false, true));
+    Reds rv;
+    const int sv = rv.add(RED_CDOT, ov, ov, nullptr, E.s);
+    const int st_ = rv.add(RED_CDOT, ov, -1, Wp, E.s);
+    const int offv = E.lin(Lv, rv);
+    E.coef(PH_LQ_COEF2, offv + sv, offw + sw, offv + st_);
+    // directions, iterate, residual, normalised next Lanczos block
+    Lin U(E.n, E.s);
+    const int od = U.out(D2), oad = U.out(AD2), ox = U.out(c.X), orr = U.out(R), ovn = U.out(Vp);
+    U.blk(od, V, dg(E.slot(SL_CV)));
+    U.blk(od, D2, dg(E.slot(SL_CD2)));
+    U.blk(od, D1, dg(E.slot(SL_CD1)));
+    U.blk(oad, Y, dg(E.slot(SL_CV)));
+    U.blk(oad, AD2, dg(E.slot(SL_CD2)));
+    U.blk(oad, AD1, dg(E.slot(SL_CD1)));
+    U.blk(ox, c.X);
+    U.reg(ox, od, dg(E.slot(SL_TAU)));
+    U.blk(orr, R);
+    U.reg(orr, oad, dg(E.slot(SL_NTAU)));
+    U.blk(ovn, Vp, dg(E.slot(SL_INVRHO)));
+    Reds r2;
+    const int s2 = r2.add(RED_NORM2, orr, -1, nullptr, E.s);
+    const int o2 = E.lin(U, r2);
+    Lin Wn(E.n, E.s);
+    const int own = Wn.out(Wp);
+    Wn.blk(own, Wp, dg(E.slot(SL_INVXI)));
+    E.lin(Wn);
+    E.coef(PH_LQ_MON, o2 + s2);
+    std::swap(V, Vp);
+    std::swap(W, Wp);
+    std::swap(D1, D2);
+    std::swap(AD1, AD2);
+    if (poll(it + 1)) break;
+  }
+}
+
 template <typename T>
 void run_bl_qmr(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
   Engine<T>& E = c.E;
@@ -1278,6 +1381,7 @@ void run_bl_qmr(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
 int blocks_needed(int method) {
   switch (method) {
     case KRM_GL_QMR: return 12;
+    case KRM_LI_QMR: return 12;
     case KRM_BL_QMR: return 11;
     case KRM_EGL_QMR: return 8;
     case KRM_BL_BICG_RQ: return 8;
@@ -1336,6 +1440,7 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
     case KRM_EGL_BICG: run_egl_bicg<T>(c, in.maxit, poll); break;
     case KRM_LI_BICG: run_li_bicg<T>(c, in.maxit, poll); break;
     case KRM_LI_BICGSTAB: run_li_bicgstab<T>(c, in.maxit, poll); break;
+    case KRM_LI_QMR: run_li_qmr<T>(c, in.maxit, poll); break;
     case KRM_BL_BICG: run_bl_bicg<T>(c, in.maxit, poll); break;
     case KRM_BL_BICG_RQ: run_bl_bicg_rq<T>(c, in.maxit, poll); break;
     case KRM_GL_BICGSTAB: run_gl_bicgstab<T>(c, in.maxit, poll); break;

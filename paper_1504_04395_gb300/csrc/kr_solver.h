@@ -11,7 +11,7 @@ namespace kr {
 enum : int {
   KRM_BL_BICG = 0, KRM_BL_BICG_RQ = 1, KRM_GL_BICG = 2, KRM_EGL_BICG = 3, KRM_BL_BICGSTAB = 4,
   KRM_BL_BICGSTAB_RQ = 5, KRM_GL_BICGSTAB = 6, KRM_BL_QMR = 7, KRM_GL_QMR = 8, KRM_EGL_QMR = 9,
-  KRM_LI_BICG = 10, KRM_LI_BICGSTAB = 11, KRM_COUNT = 12
+  KRM_LI_BICG = 10, KRM_LI_BICGSTAB = 11, KRM_LI_QMR = 12, KRM_COUNT = 13
 };
 
 struct SolveIn {

@@ -155,7 +155,8 @@ def test_c64_stencil_equals_csr(kr, dims, s):
     csr.close()
 
 
-@pytest.mark.parametrize("method", ["gl_bicg", "egl_bicg", "li_bicg", "gl_bicgstab", "li_bicgstab", "egl_qmr"])
+@pytest.mark.parametrize("method", ["gl_bicg", "egl_bicg", "li_bicg", "gl_bicgstab", "li_bicgstab", "egl_qmr",
+                                    "li_qmr"])
 def test_mixed_solve_with_and_without_pairs(kr, method):
     """FP64 defect correction over complex64 inner solves converges to the FP64 tolerance on
     both complex64 kernel variants, to the solution of a direct sparse LU."""

@@ -19,7 +19,7 @@ from workloads import ConvDiff, convdiff_csr, gaussian_block, random_csr  # noqa
 pytestmark = pytest.mark.gpu
 
 METHODS = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "li_bicg", "bl_bicgstab", "bl_bicgstab_rq",
-           "gl_bicgstab", "li_bicgstab", "gl_qmr", "egl_qmr", "bl_qmr"]
+           "gl_bicgstab", "li_bicgstab", "gl_qmr", "egl_qmr", "bl_qmr", "li_qmr"]
 HIST_RTOL = 1e-10   # per-iteration residual norms, first 20 iterations
 X_RTOL = 1e-8       # final iterate
 SENS_FACTOR = 10.0  # allowed multiple of the oracle's own rounding sensitivity
