@@ -48,8 +48,14 @@ def source_digest() -> str:
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(f.encode())
                 h.update(fh.read())
-    h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS).encode())
+    h.update(_flags_for_digest().encode())
     return h.hexdigest()
+
+
+def _flags_for_digest() -> str:
+    """The compile flags with the include directory written relative to the repository, so
+    that the same sources and flags hash alike on every machine."""
+    return " ".join(ARCH_FLAGS + [("-Iinclude" if f == "-I" + INCLUDE else f) for f in NVCC_FLAGS])
 
 
 def kernel_digest(files) -> str:
@@ -60,7 +66,7 @@ def kernel_digest(files) -> str:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
-    h.update(" ".join(ARCH_FLAGS + NVCC_FLAGS).encode())
+    h.update(_flags_for_digest().encode())
     return h.hexdigest()
 
 
