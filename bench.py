@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--operator", choices=("lattice", "csr"), default="lattice",
                     help="config-4 operator: matrix-free lattice (kr_op_create_lattice4d) or its CSR storage")
+    ap.add_argument("--config1", action="store_true",
+                    help="time to 1e-8 per method on the 2D 32x32 problem (s = 4), eager launches vs CUDA-graph replay")
     ap.add_argument("--config3", action="store_true",
                     help="time to 1e-8 per method on the 4D lattice (16^4 x 12, s = 12 point sources and 12 Gaussian)")
     ap.add_argument("--config4", action="store_true",
@@ -549,6 +551,45 @@ def config4(args):
     A.close()
 
 
+def config1(args):
+    """Config 1 (2D convection-diffusion 32 x 32, n = 1024, Pe 0.5, shift 0.1i, s = 4 Gaussian RHS,
+    seed 0, X0 = 0, relative residual 1e-8): time to tolerance per method with eager launches and
+    with the iterations replayed as a CUDA graph.  At this size a kernel takes a few
+    microseconds, so launch overhead, not the GPU, sets the pace without graphs."""
+    import statistics
+    import torch
+    from workloads import ConvDiff, convdiff_csr, gaussian_block
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as kr
+    op = ConvDiff((32, 32), (0.5, 0.5), 0.1j)
+    rp, ci, v = convdiff_csr(op)
+    A = kr.Operator(op.n, rp, ci, v)
+    B = torch.from_numpy(gaussian_block(op.n, 4, seed=0)).cuda()
+    out = {"workload": "2D convection-diffusion 32^2 (n=1024), Pe 0.5, shift 0.1i, s=4 Gaussian RHS, to 1e-8",
+           "results": {}}
+    methods = ["bl_bicg", "bl_bicg_rq", "gl_bicg", "egl_bicg", "bl_bicgstab", "gl_bicgstab", "bl_qmr", "egl_qmr"]
+    for method in methods:
+        row = {}
+        for mode in ("off", "on"):
+            kr.kr_solve(A, method, B, torch.zeros_like(B), tol=1e-8, maxit=1000, graphs=mode)
+            times = []
+            for _ in range(5):
+                X = torch.zeros_like(B)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, inf = kr.kr_solve(A, method, B, X, tol=1e-8, maxit=1000, graphs=mode)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            row["time_to_tol_ms_graphs_" + mode] = 1000 * statistics.median(times)
+            row["iters"] = inf.iters
+            row["status"] = inf.status
+        row["graph_speedup"] = row["time_to_tol_ms_graphs_off"] / row["time_to_tol_ms_graphs_on"]
+        out["results"][method] = row
+    print(json.dumps(out))
+    A.close()
+
+
 def config3(args):
     """Time to a relative residual of 1e-8 per method on the 4D lattice operator, 16^4 sites x 12
     (n = 786,432), s = 12 point sources at one seeded site and s = 12 Gaussian right-hand sides:
@@ -603,6 +644,9 @@ def main():
     args = parse_args()
     if args.cpu_sample_worker:
         cpu_sample_worker(args)
+        return
+    if args.config1:
+        config1(args)
         return
     if args.config3:
         config3(args)

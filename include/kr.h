@@ -96,6 +96,12 @@ typedef struct {
   int32_t host_buffers;   /* 1: B and X are host pointers (copied to and from the device inside the call) */
   double* history;        /* optional host array of maxit+1 doubles: ||R_k||_F / ||R_0||_F, k = 0..iters */
   double time_limit_s;    /* optional wall-clock limit (0 = none) -> KR_TIMEOUT */
+  int32_t graphs;         /* CUDA-graph replay of the iterations: 0 = automatic (on when n*s <= 2^22,
+                             where kernel launches rather than kernels take the time), 1 = on, 2 = off.
+                             Two iterations are captured once and replayed until convergence; the
+                             results are bitwise those of the eager launches.  Off while the launch
+                             profile times kernels. */
+  int32_t reserved;
 } kr_options;
 
 typedef struct {

@@ -31,6 +31,9 @@ RED = {"gram": 1, "trace": 2, "sumv": 3, "norm2": 4}
 FP64, FP32_REFINE = 0, 1
 
 
+GRAPHS = {"auto": 0, "on": 1, "off": 2}
+
+
 class KrOptions(ctypes.Structure):
     _fields_ = [
         ("tol", ctypes.c_double),
@@ -44,6 +47,8 @@ class KrOptions(ctypes.Structure):
         ("host_buffers", ctypes.c_int32),
         ("history", ctypes.POINTER(ctypes.c_double)),
         ("time_limit_s", ctypes.c_double),
+        ("graphs", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -397,7 +402,7 @@ class SolveInfo:
 
 
 def _options(tol, maxit, precision, inner_tol, max_outer, shadow, shadow_mode, check_every, host_buffers,
-             history, time_limit_s):
+             history, time_limit_s, graphs=0):
     o = KrOptions()
     lib().kr_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -411,11 +416,12 @@ def _options(tol, maxit, precision, inner_tol, max_outer, shadow, shadow_mode, c
     o.host_buffers = int(host_buffers)
     o.history = history
     o.time_limit_s = float(time_limit_s)
+    o.graphs = int(graphs)
     return o
 
 
 def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, shadow, shadow_conj, check_every,
-           stream, time_limit_s):
+           stream, time_limit_s, graphs=0):
     torch = _torch()
     n, s = B.shape
     host = not B.is_cuda
@@ -437,7 +443,8 @@ def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, sh
         mode, sptr = 2, _dev_ptr(shadow, "shadow", torch.complex128)
     elif shadow_conj:
         mode = 1
-    o = _options(tol, maxit, precision, inner_tol, max_outer, sptr, mode, check_every, host, hist, time_limit_s)
+    o = _options(tol, maxit, precision, inner_tol, max_outer, sptr, mode, check_every, host, hist, time_limit_s,
+                 GRAPHS[graphs] if isinstance(graphs, str) else int(graphs))
     info = KrInfo()
     st = fn(op.handle, method_id(method), s, bptr, xptr, ctypes.byref(o), _stream(stream), ctypes.byref(info))
     _check(st, allow_iteration_status=True)
@@ -450,17 +457,21 @@ def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, sh
 
 
 def kr_solve(op: Operator, method, B, X=None, tol=1e-8, maxit=500, precision=FP64, inner_tol=1e-4, max_outer=30,
-             shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0):
-    """Solve A X = B (B: n x s complex128, CUDA or CPU tensor; X holds X_0, default 0)."""
+             shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0, graphs="auto"):
+    """Solve A X = B (B: n x s complex128, CUDA or CPU tensor; X holds X_0, default 0).
+
+    graphs: "auto" (CUDA-graph replay of the iterations for small problems), "on" or "off".
+    """
     return _solve(lib().kr_solve, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, shadow,
-                  shadow_conj, check_every, stream, time_limit_s)
+                  shadow_conj, check_every, stream, time_limit_s, graphs)
 
 
 def kr_adjoint_solve(op: Operator, method, G, Lam=None, tol=1e-8, maxit=500, precision=FP64, inner_tol=1e-4,
-                     max_outer=30, shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0):
+                     max_outer=30, shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0,
+                     graphs="auto"):
     """Solve A^H Lambda = G with the same simultaneous methods."""
     return _solve(lib().kr_adjoint_solve, op, method, G, Lam, tol, maxit, precision, inner_tol, max_outer, shadow,
-                  shadow_conj, check_every, stream, time_limit_s)
+                  shadow_conj, check_every, stream, time_limit_s, graphs)
 
 
 def kr_grad_values(op: Operator, Lam, X, stream=None):

@@ -525,6 +525,7 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   if (!(opt.tol >= 0.0) || opt.maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return KR_BAD_ARG; }
   if (opt.shadow_mode == KR_SHADOW_USER && !opt.shadow) { set_error("user shadow is NULL"); return KR_BAD_ARG; }
   if (opt.precision != KR_FP64 && opt.precision != KR_FP32_REFINE) { set_error("unknown precision"); return KR_BAD_ARG; }
+  if (opt.graphs < 0 || opt.graphs > 2) { set_error("graphs must be 0 (automatic), 1 (on) or 2 (off)"); return KR_BAD_ARG; }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
@@ -552,6 +553,7 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   in.shadow_mode = opt.shadow_mode;
   in.shadow = opt.shadow;
   in.time_limit_s = opt.time_limit_s;
+  in.graphs = (opt.graphs == 1 || (opt.graphs == 0 && (int64_t)o.n * s <= ((int64_t)1 << 22))) ? 1 : 0;
   kr_info inf{};
   if (opt.precision == KR_FP64) {
     SolveOut so = run_solve<double>(o, method, s, dB, dX, in, st, adjoint);

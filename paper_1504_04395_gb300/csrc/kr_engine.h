@@ -165,6 +165,8 @@ struct Workspace {
   double* hist = nullptr;
   int hist_cap = 0;
   void* colbuf = nullptr;  // one column of a block (Gram fallback for s > 16)
+  cudaStream_t gstream = nullptr;  // private stream for CUDA-graph capture and replay
+  cudaEvent_t gevent = nullptr;    // orders the caller's stream and the private stream
   ~Workspace();
 };
 

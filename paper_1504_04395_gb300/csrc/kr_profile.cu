@@ -59,6 +59,8 @@ void drain(ProfState& p) {
 
 }  // namespace
 
+bool prof_active() { return P().on; }
+
 ProfToken prof_begin(int cls, cudaStream_t st) {
   ProfState& p = P();
   ProfToken t;

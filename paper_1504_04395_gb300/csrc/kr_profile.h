@@ -18,6 +18,7 @@ struct ProfToken {
 };
 
 ProfToken prof_begin(int cls, cudaStream_t st);
+bool prof_active();  // launch counting (and timing) on
 void prof_end(ProfToken& t, cudaStream_t st, double flops, double bytes);
 
 double red_flops(const RedSet& rs, int64_t n, int s);

@@ -16,6 +16,7 @@
 #include <functional>
 
 #include "kr_engine.h"
+#include "kr_profile.h"
 #include "kr_solver.h"
 
 namespace kr {
@@ -47,6 +48,8 @@ Workspace::~Workspace() {
   for (void* p : blocks) cudaFree(p);
   for (void* p : vecs) cudaFree(p);
   cudaFree(partials); cudaFree(red); cudaFree(arena); cudaFree(st); cudaFree(hist); cudaFree(colbuf);
+  if (gevent) cudaEventDestroy(gevent);
+  if (gstream) cudaStreamDestroy(gstream);
 }
 
 template <>
@@ -1405,9 +1408,31 @@ int matvecs_per_iter(int method, int s) {
 // driver for one precision
 // =========================================================================================
 template <typename T>
-SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, const SolveIn& in, cudaStream_t st,
+SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, const SolveIn& in, cudaStream_t user_st,
                    bool adjoint) {
   Workspace& ws = get_workspace(op, s, sizeof(C2<T>), blocks_needed(method), vecs_needed(method), in.maxit);
+  // CUDA-graph replay: iteration 0 runs eagerly (it also makes every lazy allocation), the
+  // launches of iterations 1 and 2 are captured on a private stream (the caller's may be the
+  // legacy default stream, which cannot be captured), and the graph is replayed until the
+  // device state says done.  The launch profile counts launches on the host, so it disables it.
+  const bool graphs = in.graphs && in.maxit >= 3 && !prof_active();
+  cudaStream_t st = user_st;
+  if (graphs) {
+    if (!ws.gstream) KR_CUDA(cudaStreamCreateWithFlags(&ws.gstream, cudaStreamNonBlocking));
+    if (!ws.gevent) KR_CUDA(cudaEventCreateWithFlags(&ws.gevent, cudaEventDisableTiming));
+    KR_CUDA(cudaEventRecord(ws.gevent, user_st));
+    KR_CUDA(cudaStreamWaitEvent(ws.gstream, ws.gevent, 0));
+    st = ws.gstream;
+  }
+  struct CaptureGuard {  // ends a capture left open by an exception
+    cudaStream_t s = nullptr;
+    ~CaptureGuard() {
+      if (s) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamEndCapture(s, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+      }
+    }
+  } guard;
   Engine<T> E(op, adjoint, s, st, ws);
   DevState h{};
   h.maxit = in.maxit;
@@ -1423,8 +1448,8 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
   const auto t0 = std::chrono::steady_clock::now();
   bool timed_out = false;
   const int every = in.check_every > 0 ? in.check_every : 8;
-  std::function<bool(int)> poll = [&](int it) -> bool {
-    if (it % every != 0 && it < in.maxit) return false;
+  // read the device state back; true when the iteration must stop
+  auto check = [&]() -> bool {
     KR_CUDA(cudaMemcpyAsync(pin, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
     KR_CUDA(cudaStreamSynchronize(st));
     if (pin->done) return true;
@@ -1433,6 +1458,38 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
       if (el > in.time_limit_s) { timed_out = true; return true; }
     }
     return false;
+  };
+  std::function<bool(int)> poll = [&](int it) -> bool {
+    if (graphs) {
+      if (it == 1) {
+        KR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        guard.s = st;
+        return false;
+      }
+      if (it == 2) return false;
+      // it == 3: iterations 1 and 2 are recorded, not run; replay them in pairs
+      cudaGraph_t g = nullptr;
+      guard.s = nullptr;
+      KR_CUDA(cudaStreamEndCapture(st, &g));
+      cudaGraphExec_t ge = nullptr;
+      const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      KR_CUDA(e);
+      const int per_check = every >= 4 ? every / 2 : 1;
+      int launched = 1, replays = 0;  // iterations launched so far
+      bool stop = false;
+      while (!stop) {
+        const cudaError_t le = cudaGraphLaunch(ge, st);
+        if (le != cudaSuccess) { cudaGraphExecDestroy(ge); KR_CUDA(le); }
+        launched += 2;
+        ++replays;
+        if (launched >= in.maxit || replays % per_check == 0) stop = check() || launched >= in.maxit;
+      }
+      cudaGraphExecDestroy(ge);
+      return true;
+    }
+    if (it % every != 0 && it < in.maxit) return false;
+    return check();
   };
   Ctx<T> c{E, B, X, in.shadow, in.shadow_mode, 0};
   switch (method) {
@@ -1461,6 +1518,10 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
   o.matvecs = pin->iter * matvecs_per_iter(method, s);
   o.hist.resize(pin->iter + 1);
   KR_CUDA(cudaMemcpy(o.hist.data(), ws.hist, sizeof(double) * (pin->iter + 1), cudaMemcpyDeviceToHost));
+  if (graphs) {  // later work on the caller's stream follows the solve
+    KR_CUDA(cudaEventRecord(ws.gevent, st));
+    KR_CUDA(cudaStreamWaitEvent(user_st, ws.gevent, 0));
+  }
   return o;
 }
 

@@ -22,6 +22,7 @@ struct SolveIn {
   const void* shadow = nullptr;
   double time_limit_s = 0.0;
   int stall = 0;  // > 0: stop when above the starting residual with no new minimum for max(stall, best_iter) iterations
+  int graphs = 0;  // replay the iterations as a CUDA graph
 };
 
 struct SolveOut {
