@@ -178,3 +178,73 @@ def test_lattice_operator_rejects_unsupported_calls(kr):
     with pytest.raises(kr.KrylovError):
         kr.kr_op_update_values(op, v)
     op.close()
+
+
+def _lattice_rows_by_definition(dims, diag, hop, links, V_nb, sites_idx, spins, colours):
+    """Rows (x, a, c) of A V from the operator's definition, entry by entry:
+    y = d v_x + hop sum_mu [ (I - gamma_mu) (x) U_mu(x) v_{x+mu} + (I + gamma_mu) (x) U_mu(x-mu)^H v_{x-mu} ].
+    V_nb(x) returns the (4, 3, s) block of V at site x."""
+    strides = [1, dims[0], dims[0] * dims[1], dims[0] * dims[1] * dims[2]]
+    eye = np.eye(4)
+    out = []
+    for x, a, c in zip(sites_idx, spins, colours):
+        coords, rem = [], x
+        for L in dims:
+            coords.append(rem % L)
+            rem //= L
+        y = diag * V_nb(x)[a, c]
+        for mu in range(4):
+            fw = x + (((coords[mu] + 1) % dims[mu]) - coords[mu]) * strides[mu]
+            bw = x + (((coords[mu] - 1) % dims[mu]) - coords[mu]) * strides[mu]
+            Pf = eye - GAMMA[mu]
+            Pb = eye + GAMMA[mu]
+            Vf, Vb = V_nb(fw), V_nb(bw)
+            for b in range(4):
+                for cp in range(3):
+                    y = y + hop * Pf[a, b] * links[mu, x, c, cp] * Vf[b, cp]
+                    y = y + hop * Pb[a, b] * np.conj(links[mu, bw, cp, c]) * Vb[b, cp]
+        out.append(y)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_lattice_full_size_sampled_rows(kr, dtype):
+    """Config-4 size (24^4 x 12, n = 3,981,312), s = 32, the launch the mixed-precision bench
+    times: 400 sampled rows (and the first and last) recomputed from the operator's definition."""
+    dims = (24, 24, 24, 24)
+    sites = 24 ** 4
+    n = 12 * sites
+    s = 32
+    U = haar_links(dims, 0)
+    op = kr.Operator.lattice4d(dims, 4.0 + LATTICE_MASS, -0.5, GAMMA, U)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    V = torch.complex(torch.randn(n, s, device="cuda", generator=g, dtype=torch.float64),
+                      torch.randn(n, s, device="cuda", generator=g, dtype=torch.float64))
+    if dtype == "c64":
+        V32 = V.to(torch.complex64)
+        Y, _ = kr.kr_op_apply_reduce_c64(op, V32)
+        V = V32.to(torch.complex128)
+        Uref = c64(U * -0.5) / -0.5  # the kernel multiplies by the hop-scaled links rounded to complex64
+    else:
+        Y = kr.kr_op_apply(op, V)
+        Uref = U
+    rng = np.random.default_rng(24)
+    rows = np.concatenate([rng.integers(0, n, 400), [0, n - 1]])
+    xs, rem = rows // 12, rows % 12
+    a_s, c_s = rem // 3, rem % 3
+    Vsite = V.view(sites, 4, 3, s)
+
+    cache = {}
+
+    def V_nb(x):
+        if x not in cache:
+            cache[x] = Vsite[int(x)].cpu().numpy()
+        return cache[x]
+
+    ref = _lattice_rows_by_definition(dims, 4.0 + LATTICE_MASS, -0.5, Uref, V_nb, xs, a_s, c_s)
+    got = Y[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.complex128)
+    # scale: a bound on the sum of |terms| per entry (diagonal 2.2 |v|, 48 hop terms <= |v| / 2)
+    scale = 50 * float(V.abs().max())
+    u = U32 if dtype == "c64" else U64
+    assert np.all(np.abs(got - ref) <= 64 * u * scale), np.max(np.abs(got - ref) / scale)
+    op.close()
