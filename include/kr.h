@@ -162,6 +162,28 @@ KR_API kr_status kr_op_create_stencil(int32_t dim, const int64_t* dims, const do
 KR_API kr_status kr_op_create_lattice4d(const int64_t* dims, const double* diag, double hop, const double* gamma,
                                         const double* links, int32_t device, kr_op* out);
 
+/* Preconditioners (kr_op_set_preconditioner). */
+typedef enum {
+  KR_PREC_NONE = 0,
+  KR_PREC_ILU0 = 1  /* incomplete LU without fill-in (Sec. 5, second set of experiments) */
+} kr_preconditioner;
+
+/* Set (or with KR_PREC_NONE remove) a right preconditioner of a CSR operator: later kr_solve
+ * calls solve A M^{-1} Y = B - A X_0 from Y = 0 and return X = X_0 + M^{-1} Y, with every
+ * iteration's products A M^{-1} V and M^{-H} A^H W (the methods are unchanged; the reported
+ * residuals are those of the original system).  ILU(0): M = L U, L unit lower and U upper
+ * triangular with the sparsity pattern of A and (L U)_ij = A_ij on it, factorised once in
+ * FP64 on the host; each triangular solve is level-scheduled (one launch per level of row
+ * dependencies).  Requires every diagonal entry stored; KR_BREAKDOWN on a zero pivot;
+ * KR_UNSUPPORTED for matrix-free operators.  kr_adjoint_solve and KR_FP32_REFINE return
+ * KR_UNSUPPORTED while a preconditioner is set.  kr_op_update_values removes it. */
+KR_API kr_status kr_op_set_preconditioner(kr_op op, int32_t kind);
+
+/* Y = M^{-1} V (adjoint = 0) or M^{-H} V (adjoint = 1) with the operator's preconditioner;
+ * V, Y: device n x s complex128 blocks (Y may equal V). */
+KR_API kr_status kr_op_apply_precond(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y,
+                                     void* stream);
+
 /* Replace the stored entries of A (same sparsity pattern, same order as given to
  * kr_op_create_csr): vals[2*nnz] interleaved (re, im), a host pointer
  * (on_device = 0) or a device pointer (on_device != 0).  A^H, the real/complex

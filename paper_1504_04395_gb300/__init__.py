@@ -101,6 +101,8 @@ SIGNATURES = {
     "kr_block_reduce_noalloc": (_I32, [_I64, _I32, _P, _P, _I32, _P, _P]),
     "kr_profile_enable": (_I32, [_I32, _I32]),
     "kr_set_column_pairs": (_I32, [_I32]),
+    "kr_op_set_preconditioner": (_I32, [_P, _I32]),
+    "kr_op_apply_precond": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "kr_set_lattice_rows_per_thread": (_I32, [_I32]),
     "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
 }
@@ -238,6 +240,11 @@ class Operator:
         self.nnz = self.info()["nnz"]
         return self
 
+    def set_preconditioner(self, kind="ilu0"):
+        """Right preconditioner for later kr_solve calls: "ilu0" or None (kr_op_set_preconditioner)."""
+        _check(lib().kr_op_set_preconditioner(self.handle, {None: 0, "none": 0, "ilu0": 1}[kind]))
+        return self
+
     def __init__(self, n, rowptr, colidx, vals, device=None):
         torch = _torch()
         if device is None:
@@ -357,6 +364,17 @@ def kr_block_reduce_c64(U, Y, kind="gram", stream=None):
     _check(lib().kr_block_reduce_c64(n, s, uptr, _dev_ptr(Y, "Y", torch.complex64), k, _dev_ptr(out, "out"),
                                      _stream(stream)))
     return out
+
+
+def kr_op_apply_precond(op: Operator, V, Y=None, adjoint=False, stream=None):
+    """Y = M^{-1} V (or M^{-H} V) with the operator's preconditioner (complex128 device blocks)."""
+    torch = _torch()
+    s = V.shape[1]
+    if Y is None:
+        Y = torch.empty_like(V)
+    _check(lib().kr_op_apply_precond(op.handle, int(adjoint), s, _dev_ptr(V, "V", torch.complex128, (op.n, s)),
+                                     _dev_ptr(Y, "Y", torch.complex128, (op.n, s)), _stream(stream)))
+    return Y
 
 
 def kr_block_reduce_noalloc(U, Y, out, kind="gram", stream=None):
@@ -514,5 +532,5 @@ __all__ = [
     "METHODS", "STATUS", "Operator", "SolveInfo", "KrylovError", "lib", "load_library",
     "kr_op_create_csr", "kr_op_update_values", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
-    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_set_lattice_rows_per_thread", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
+    "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_op_apply_precond", "kr_set_lattice_rows_per_thread", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
 ]

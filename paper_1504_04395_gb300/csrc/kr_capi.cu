@@ -9,6 +9,7 @@
 
 #include "../../include/kr.h"
 #include "kr_engine.h"
+#include "kr_precond.h"
 #include "kr_profile.h"
 #include "kr_solver.h"
 
@@ -41,6 +42,12 @@ namespace {
 __global__ void to_c64_kernel(const double2* __restrict__ a, float2* __restrict__ b, int64_t cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void add_c128_kernel(double2* __restrict__ x, const double2* __restrict__ d, int64_t cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i].x += d[i].x;
+    x[i].y += d[i].y;
+  }
 }
 __global__ void add_c64_kernel(double2* __restrict__ x, const float2* __restrict__ d, int64_t cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
@@ -359,6 +366,43 @@ kr_status kr_op_create_lattice4d(const int64_t* dims, const double* diag, double
   KR_API_END
 }
 
+kr_status kr_op_set_preconditioner(kr_op op, int32_t kind) {
+  if (!op) { set_error("op is NULL"); return KR_BAD_ARG; }
+  if (kind != KR_PREC_NONE && kind != KR_PREC_ILU0) { set_error("unknown preconditioner"); return KR_BAD_ARG; }
+  if (kind == KR_PREC_ILU0 && (op->op.stA.d > 0 || op->op.lat.on)) {
+    set_error("ILU(0) needs a CSR operator");
+    return KR_UNSUPPORTED;
+  }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  KR_CUDA(cudaDeviceSynchronize());
+  o.ilu.free_all();
+  if (kind == KR_PREC_NONE) return KR_OK;
+  const int r = build_ilu0(o);
+  if (r != KR_OK) {
+    o.ilu.free_all();
+    set_error(r == KR_BREAKDOWN ? "ILU(0): zero pivot" : "ILU(0): a diagonal entry is missing or an entry repeated");
+    return static_cast<kr_status>(r);
+  }
+  return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_op_apply_precond(kr_op op, int32_t adjoint, int32_t s, const double* V, double* Y, void* stream) {
+  if (!op || !V || !Y || bad_s(s)) { set_error("invalid op, V, Y or s"); return KR_BAD_ARG; }
+  if (!op->op.ilu.on) { set_error("no preconditioner set"); return KR_BAD_ARG; }
+  KR_API_BEGIN
+  Operator& o = op->op;
+  KR_CUDA(cudaSetDevice(o.device));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Workspace& ws = get_workspace(o, s, 24, 4, 0, 1);
+  apply_ilu0(o, adjoint != 0, s, reinterpret_cast<const double2*>(V), reinterpret_cast<double2*>(Y),
+             reinterpret_cast<double2*>(ws.blocks[3]), st);
+  return KR_OK;
+  KR_API_END
+}
+
 kr_status kr_op_update_values(kr_op op, const double* vals, int32_t on_device) {
   if (!op || (!vals && op->op.nnz > 0)) { set_error("op and vals must be non-NULL"); return KR_BAD_ARG; }
   if (op->op.stA.d > 0 || op->op.lat.on) { set_error("matrix-free operators have no CSR values"); return KR_UNSUPPORTED; }
@@ -526,6 +570,10 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   if (opt.shadow_mode == KR_SHADOW_USER && !opt.shadow) { set_error("user shadow is NULL"); return KR_BAD_ARG; }
   if (opt.precision != KR_FP64 && opt.precision != KR_FP32_REFINE) { set_error("unknown precision"); return KR_BAD_ARG; }
   if (opt.graphs < 0 || opt.graphs > 2) { set_error("graphs must be 0 (automatic), 1 (on) or 2 (off)"); return KR_BAD_ARG; }
+  if (op->op.ilu.on && (adjoint || opt.precision != KR_FP64)) {
+    set_error("the ILU(0) preconditioner is supported for kr_solve in FP64");
+    return KR_UNSUPPORTED;
+  }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
@@ -553,9 +601,38 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   in.shadow_mode = opt.shadow_mode;
   in.shadow = opt.shadow;
   in.time_limit_s = opt.time_limit_s;
-  in.graphs = (opt.graphs == 1 || (opt.graphs == 0 && (int64_t)o.n * s <= ((int64_t)1 << 22))) ? 1 : 0;
+  // automatic graphs: small problems, and every preconditioned solve (one launch per level of the
+  // triangular solves makes those iterations launch-bound)
+  in.graphs = (opt.graphs == 1 || (opt.graphs == 0 && ((int64_t)o.n * s <= ((int64_t)1 << 22) || o.ilu.on))) ? 1 : 0;
   kr_info inf{};
-  if (opt.precision == KR_FP64) {
+  if (opt.precision == KR_FP64 && o.ilu.on) {
+    // right preconditioning: A M^{-1} Y = B - A X0 from Y = 0, then X = X0 + M^{-1} Y
+    Workspace& rw = get_workspace(o, s, 24, 4, 0, 1);
+    void *R0 = rw.blocks[0], *Yb = rw.blocks[1], *Tb = rw.blocks[2];
+    const int64_t cnt = o.n * (int64_t)s;
+    const double res0 = true_residual(o, s, dB, dX, R0, st, false);
+    KR_CUDA(cudaMemsetAsync(Yb, 0, sizeof(double2) * cnt, st));
+    SolveIn pin = in;
+    pin.precond = 1;
+    SolveOut so = run_solve<double>(o, method, s, R0, Yb, pin, st, false);
+    apply_ilu0(o, false, s, reinterpret_cast<const double2*>(Yb), reinterpret_cast<double2*>(Yb),
+               reinterpret_cast<double2*>(Tb), st);
+    {
+      ProfToken tk = prof_begin(KC_OTHER, st);
+      add_c128_kernel<<<grid1d(cnt), 256, 0, st>>>(reinterpret_cast<double2*>(dX),
+                                                    reinterpret_cast<const double2*>(Yb), cnt);
+      KR_CUDA(cudaGetLastError());
+      prof_end(tk, st, 2.0 * cnt, 48.0 * cnt);
+    }
+    inf.iters = so.iters;
+    inf.matvecs = so.matvecs;
+    inf.status = so.status;
+    inf.relres_recursive = so.relres_recursive;
+    const double tr = true_residual(o, s, dB, dX, nullptr, st, false);
+    inf.relres_true = res0 > 0 ? tr / res0 : tr;
+    if (opt.history)
+      for (size_t k = 0; k < so.hist.size() && (int)k <= opt.maxit; ++k) opt.history[k] = so.hist[k];
+  } else if (opt.precision == KR_FP64) {
     SolveOut so = run_solve<double>(o, method, s, dB, dX, in, st, adjoint);
     inf.iters = so.iters;
     inf.matvecs = so.matvecs;

@@ -121,9 +121,29 @@ struct LatticeSpec {
   std::vector<double> h_links; // host copy (interleaved re, im), scaled
 };
 
+// one triangular factor of the ILU(0) preconditioner on the device (kr_precond.cu)
+struct TriDev {
+  int64_t n = 0, h_nnz = 0;
+  int nlev = 0;
+  std::vector<int64_t> h_lev_ptr;  // host: first row of each level in lev_rows
+  int64_t* rowptr = nullptr;       // off-diagonal entries (CSR)
+  int32_t* colidx = nullptr;
+  double2* vals = nullptr;
+  double2* invdiag = nullptr;      // inverse diagonal; null: unit diagonal
+  int32_t* lev_rows = nullptr;     // rows ordered by level
+  void free_all();
+};
+
+struct IluDev {
+  bool on = false;
+  TriDev L, U, UH, LH;  // M = L U; M^{-H} = L^{-H} U^{-H}
+  void free_all();
+};
+
 struct Operator {
   int device = 0;
   LatticeSpec lat;
+  IluDev ilu;  // ILU(0) right preconditioner (kr_op_set_preconditioner)
   int64_t n = 0, nnz = 0;
   int real_offdiag = 0;
   StencilSpec stA, stAH;     // matrix-free operator (and its adjoint) when stA.d > 0
@@ -165,6 +185,7 @@ struct Workspace {
   double* hist = nullptr;
   int hist_cap = 0;
   void* colbuf = nullptr;  // one column of a block (Gram fallback for s > 16)
+  void* ptmp[2] = {nullptr, nullptr};  // preconditioner scratch blocks
   cudaStream_t gstream = nullptr;  // private stream for CUDA-graph capture and replay
   cudaEvent_t gevent = nullptr;    // orders the caller's stream and the private stream
   ~Workspace();

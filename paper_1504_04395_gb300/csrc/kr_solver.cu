@@ -16,6 +16,7 @@
 #include <functional>
 
 #include "kr_engine.h"
+#include "kr_precond.h"
 #include "kr_profile.h"
 #include "kr_solver.h"
 
@@ -40,6 +41,7 @@ Operator::~Operator() {
   A.free_all(); AH.free_all(); A32.free_all(); AH32.free_all();
   cudaFree(orig_rowptr); cudaFree(orig_colidx);
   cudaFree(lat.links); cudaFree(lat.links32);
+  ilu.free_all();
   if (pinned) cudaFreeHost(pinned);
   cudaSetDevice(prev);
 }
@@ -48,6 +50,7 @@ Workspace::~Workspace() {
   for (void* p : blocks) cudaFree(p);
   for (void* p : vecs) cudaFree(p);
   cudaFree(partials); cudaFree(red); cudaFree(arena); cudaFree(st); cudaFree(hist); cudaFree(colbuf);
+  cudaFree(ptmp[0]); cudaFree(ptmp[1]);
   if (gevent) cudaEventDestroy(gevent);
   if (gstream) cudaStreamDestroy(gstream);
 }
@@ -191,6 +194,7 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
 }  // namespace
 
 void rebuild_operator_values(Operator& op) {
+  op.ilu.free_all();  // factors of the old values
   const bool had32 = op.have32;
   op.A.free_all();
   op.AH.free_all();
@@ -304,6 +308,7 @@ inline Cf mat(const double2* p, bool neg = false) { Cf c; c.kind = COEF_MAT; c.p
 inline Cf dg(const double2* p, bool conj = false, bool neg = false) {
   Cf c; c.kind = COEF_DIAG; c.p = p; c.conj = conj; c.neg = neg; return c;
 }
+inline Cf real(double r) { Cf c; c.kind = COEF_REAL; c.r = r; return c; }
 
 struct Reds {
   RedSet rs{};
@@ -374,8 +379,42 @@ struct Engine {
   Workspace& ws;
   int red_top = 0;  // next free offset in ws.red for this iteration's reductions
 
+  bool prec = false;  // right preconditioning: the products are A M^{-1} and M^{-H} A^H
+
   Engine(Operator& o, bool sw, int s_, cudaStream_t stream, Workspace& w)
       : op(o), swap(sw), s(s_), n(o.n), st(stream), ws(w) {}
+
+  double2* ptmp(int i) {  // n x s scratch blocks of the preconditioner
+    if (!ws.ptmp[i]) KR_CUDA(cudaMalloc(&ws.ptmp[i], std::max<size_t>((size_t)n * s * sizeof(double2), 16)));
+    return reinterpret_cast<double2*>(ws.ptmp[i]);
+  }
+
+  // Y = ay op(A) V + bz Z with fused reductions (op(A) preconditioned when prec); returns red offset
+  int spmm(bool adjA, int sdim, const void* V, void* Y, Reds r = Reds{}, const void* Z = nullptr, double ay = 1.0,
+           double bz = 0.0, const double2* ys = nullptr, bool ysconj = false, bool ysneg = false) {
+    if constexpr (sizeof(T) == 8) {
+      if (prec) {
+        if (!adjA) {  // A (M^{-1} V): the input preconditioned, the product as usual
+          apply_ilu0(op, false, sdim, reinterpret_cast<const double2*>(V), ptmp(0), ptmp(1), st);
+          return spmm_op(false, sdim, ptmp(0), Y, r, Z, ay, bz, ys, ysconj, ysneg);
+        }
+        // M^{-H} (A^H V): the product, the adjoint solve, then scaling, addend and reductions
+        spmm_op(true, sdim, V, ptmp(0));
+        if (r.rs.nred == 0 && Z == nullptr && ys == nullptr && ay == 1.0) {
+          apply_ilu0(op, true, sdim, ptmp(0), reinterpret_cast<double2*>(Y), ptmp(1), st);
+          return -1;
+        }
+        apply_ilu0(op, true, sdim, ptmp(0), ptmp(0), ptmp(1), st);
+        if (ys != nullptr && ay != 1.0) throw CudaError{cudaErrorInvalidValue, "preconditioned product: ay with ys"};
+        Lin L(n, sdim);
+        const int o = L.out(Y);
+        L.blk(o, ptmp(0), ys != nullptr ? sc(ys, ysconj, ysneg) : (ay == 1.0 ? one() : real(ay)));
+        if (Z != nullptr) L.blk(o, Z, real(bz));
+        return lin(L, r);
+      }
+    }
+    return spmm_op(adjA, sdim, V, Y, r, Z, ay, bz, ys, ysconj, ysneg);
+  }
 
   const int* done() const { return &ws.st->done; }
   C2<T>* blk(int i) const { return reinterpret_cast<C2<T>*>(ws.blocks[i]); }
@@ -383,8 +422,8 @@ struct Engine {
   double2* slot(int i) const { return ws.arena + (size_t)i * kSlotElems; }
 
   // Y = ay op(A) V + bz Z, op(A) = A or A^H, with fused reductions; returns red offset
-  int spmm(bool adjA, int sdim, const void* V, void* Y, Reds r = Reds{}, const void* Z = nullptr, double ay = 1.0,
-           double bz = 0.0, const double2* ys = nullptr, bool ysconj = false, bool ysneg = false) {
+  int spmm_op(bool adjA, int sdim, const void* V, void* Y, Reds r = Reds{}, const void* Z = nullptr, double ay = 1.0,
+              double bz = 0.0, const double2* ys = nullptr, bool ysconj = false, bool ysneg = false) {
     SpmmArgs<T> a = op_spmm_args<T>(op, adjA != swap, sdim);
     a.n = n;
     a.V = reinterpret_cast<const C2<T>*>(V);
@@ -1434,6 +1473,7 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
     }
   } guard;
   Engine<T> E(op, adjoint, s, st, ws);
+  E.prec = in.precond && op.ilu.on && !adjoint;
   DevState h{};
   h.maxit = in.maxit;
   h.tol = in.tol;

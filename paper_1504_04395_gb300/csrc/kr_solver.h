@@ -23,6 +23,7 @@ struct SolveIn {
   double time_limit_s = 0.0;
   int stall = 0;  // > 0: stop when above the starting residual with no new minimum for max(stall, best_iter) iterations
   int graphs = 0;  // replay the iterations as a CUDA graph
+  int precond = 0;  // solve A M^{-1} Y = B with the operator's ILU(0) (FP64, kr_solve only)
 };
 
 struct SolveOut {
