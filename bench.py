@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--operator", choices=("lattice", "csr"), default="lattice",
                     help="config-4 operator: matrix-free lattice (kr_op_create_lattice4d) or its CSR storage")
+    ap.add_argument("--ilu", action="store_true",
+                    help="time to 1e-8 with and without ILU(0) right preconditioning on 3D convection-diffusion (--grid, --s)")
     ap.add_argument("--config1", action="store_true",
                     help="time to 1e-8 per method on the 2D 32x32 problem (s = 4), eager launches vs CUDA-graph replay")
     ap.add_argument("--config3", action="store_true",
@@ -551,6 +553,47 @@ def config4(args):
     A.close()
 
 
+def ilu_mode(args):
+    """Sec. 5's second set of experiments on the config-2 problem: 3D convection-diffusion
+    (--grid^3, Pe 0.8, shift 0.05i, --s Gaussian right-hand sides), time to a relative
+    residual of 1e-8 without and with ILU(0) right preconditioning, for the methods of
+    --methods.  The factorisation (host, FP64) is timed separately."""
+    import torch
+    from workloads import ConvDiff, convdiff_csr, gaussian_block
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as kr
+    L, s = args.grid, args.s
+    op = ConvDiff((L, L, L), (0.8, 0.8, 0.8), 0.05j)
+    rp, ci, v = convdiff_csr(op)
+    A = kr.Operator(op.n, rp, ci, v)
+    B = torch.from_numpy(gaussian_block(op.n, s, seed=0)).cuda()
+    methods = ["egl_bicg", "gl_bicg", "bl_bicgstab", "gl_bicgstab"]
+    if args.methods != ",".join(METHODS10):
+        methods = args.methods.split(",")
+    out = {"workload": "3D convection-diffusion %d^3 (n=%d), Pe 0.8, shift 0.05i, s=%d Gaussian RHS, to 1e-8"
+                       % (L, op.n, s), "results": {}}
+    for prec in (None, "ilu0"):
+        t0 = time.perf_counter()
+        A.set_preconditioner(prec)
+        torch.cuda.synchronize()
+        if prec:
+            out["ilu0_setup_s"] = time.perf_counter() - t0
+        for method in methods:
+            kr.kr_solve(A, method, B, torch.zeros_like(B), tol=1e-8, maxit=3)  # workspaces
+            X = torch.zeros_like(B)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, inf = kr.kr_solve(A, method, B, X, tol=1e-8, maxit=args.maxit)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            out["results"]["%s_%s" % (method, prec or "none")] = {
+                "time_to_tol_ms": 1000 * el, "iters": inf.iters, "status": inf.status,
+                "relres_true": inf.relres_true}
+    print(json.dumps(out))
+    A.close()
+
+
 def config1(args):
     """Config 1 (2D convection-diffusion 32 x 32, n = 1024, Pe 0.5, shift 0.1i, s = 4 Gaussian RHS,
     seed 0, X0 = 0, relative residual 1e-8): time to tolerance per method with eager launches and
@@ -644,6 +687,9 @@ def main():
     args = parse_args()
     if args.cpu_sample_worker:
         cpu_sample_worker(args)
+        return
+    if args.ilu:
+        ilu_mode(args)
         return
     if args.config1:
         config1(args)
