@@ -97,7 +97,8 @@ typedef struct {
   double* history;        /* optional host array of maxit+1 doubles: ||R_k||_F / ||R_0||_F, k = 0..iters */
   double time_limit_s;    /* optional wall-clock limit (0 = none) -> KR_TIMEOUT */
   int32_t graphs;         /* CUDA-graph replay of the iterations: 0 = automatic (on when n*s <= 2^22,
-                             where kernel launches rather than kernels take the time), 1 = on, 2 = off.
+                             where kernel launches rather than kernels take the time, and whenever a
+                             preconditioner is set), 1 = on, 2 = off.
                              Two iterations are captured once and replayed until convergence; the
                              results are bitwise those of the eager launches.  Off while the launch
                              profile times kernels. */
