@@ -50,7 +50,20 @@ template <typename T> __host__ __device__ __forceinline__ C2<T> csub(C2<T> a, C2
 template <typename T> __host__ __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
   return mk<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
-template <typename T> __host__ __device__ __forceinline__ C2<T> cconj(C2<T> a) { return mk<T>(a.x, -a.y); }
+// v or -v by a runtime flag.  For doubles the sign bit is flipped on the integer pipe: a
+// negation that cannot be folded into an FMA operand costs an FP64 add, and the FP64 pipe
+// is the scarce unit (bitwise the same result as the floating-point negation).
+__device__ __forceinline__ double neg_if(double v, bool f) {
+  return __hiloint2double(__double2hiint(v) ^ (f ? (int)0x80000000 : 0), __double2loint(v));
+}
+__device__ __forceinline__ float neg_if(float v, bool f) { return f ? -v : v; }
+template <typename T> __host__ __device__ __forceinline__ C2<T> cconj(C2<T> a) {
+#ifdef __CUDA_ARCH__
+  return mk<T>(a.x, neg_if(a.y, true));
+#else
+  return mk<T>(a.x, -a.y);
+#endif
+}
 template <typename T> __host__ __device__ __forceinline__ T cabs2(C2<T> a) { return a.x * a.x + a.y * a.y; }
 
 __device__ __forceinline__ double2 to_d2(double2 a) { return a; }

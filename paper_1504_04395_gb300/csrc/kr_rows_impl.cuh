@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
       const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
       // batches of kBatch entries: all index, value and gathered-row loads of a batch are
       // issued before its FMAs, so several neighbour rows are in flight per thread
-      constexpr int kBatch = sizeof(T) == 4 ? 4 : 1;
+      constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
       if (a.split) {
         if (act) y = cmul<T>(a.diag[j], a.V[j * s + c]);
         for (int64_t k = k0; k < k1; k += kBatch) {
@@ -348,18 +348,18 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
             } else {
               if (rowok) x = reinterpret_cast<const C2<T>*>(t.src)[j];
             }
-            if (t.xconj) x.y = -x.y;
+            x.y = neg_if(x.y, t.xconj);
             if (t.coef_kind == COEF_ONE) {
-              if (ti == 0) val = t.neg ? mk<T>(-x.x, -x.y) : x;  // leading copy: no add to zero
-              else val = t.neg ? csub<T>(val, x) : cadd<T>(val, x);
+              x = mk<T>(neg_if(x.x, t.neg), neg_if(x.y, t.neg));
+              if (ti == 0) val = x;  // leading copy: no add to zero
+              else val = cadd<T>(val, x);
             } else if (t.coef_kind == COEF_REAL) {
               val = cfmareal<T>((T)t.creal, x, val);
             } else if (t.coef_kind == COEF_SCALAR) {
               val = cfma<T>(Sc[oi * kMaxTerm + ti], x, val);
             } else if (t.coef_kind == COEF_DIAG) {
               C2<T> d = (c < s) ? Ms[t.coef_idx * ss + c] : czero<T>();
-              if (t.conj) d.y = -d.y;
-              if (t.neg) { d.x = -d.x; d.y = -d.y; }
+              d = mk<T>(neg_if(d.x, t.neg), neg_if(d.y, (t.conj != 0) != (t.neg != 0)));
               val = cfma<T>(d, x, val);
             } else {  // COEF_MAT: val += sum_a x[j][a] * M[a][c]  (or minus)
               const C2<T>* M = Ms + t.coef_idx * ss;  // negation already folded into M
