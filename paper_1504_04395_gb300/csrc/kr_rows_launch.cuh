@@ -137,13 +137,28 @@ static void lattice_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, 
 }
 
 // complex64 launches on column pairs (GP threads per row, GP = next power of two >= s/2)
+template <int GP, bool STENCIL, int NR>
+static void spmm2_launch(const SpmmArgs<float>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st,
+                         size_t smem) {
+  thread_local std::unordered_map<size_t, int> occ;
+  grid = resident_grid(spmm2_kernel<GP, STENCIL, NR>, smem, grid, occ);
+  spmm2_kernel<GP, STENCIL, NR><<<grid, kThreads, smem, st>>>(a, rs, done);
+}
+
 template <int GP>
 static void spmm2_go(const SpmmArgs<float>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(float2) : 0;
   if (smem > 48 * 1024) throw CudaError{cudaErrorInvalidValue, "spmm: too many reduction slots"};
-  thread_local std::unordered_map<size_t, int> occ;
-  grid = resident_grid(spmm2_kernel<GP>, smem, grid, occ);
-  spmm2_kernel<GP><<<grid, kThreads, smem, st>>>(a, rs, done);
+  // up to two fused reductions (every product of the global, economic and Li methods but
+  // the initial residual's) use the kernels with two accumulator slots
+  const bool two = rs.nred <= 2;
+  if (a.nst > 0) {
+    if (two) spmm2_launch<GP, true, 2>(a, rs, grid, done, st, smem);
+    else spmm2_launch<GP, true, kMaxRed>(a, rs, grid, done, st, smem);
+  } else {
+    if (two) spmm2_launch<GP, false, 2>(a, rs, grid, done, st, smem);
+    else spmm2_launch<GP, false, kMaxRed>(a, rs, grid, done, st, smem);
+  }
   KR_CUDA(cudaGetLastError());
 }
 

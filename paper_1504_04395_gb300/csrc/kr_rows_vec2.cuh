@@ -97,13 +97,15 @@ __device__ __forceinline__ Pair pzero() {
 }
 
 // accumulators of the fused reductions (kinds TRACE, SUMV, NORM2: one value; CDOT: one per column)
+template <int NR = kMaxRed>
 struct Acc2 {
-  float2 v[kMaxRed][2];
+  float2 v[NR][2];
 };
 
-__device__ __forceinline__ void red2_add(const RedSpec& r, int ri, Acc2& acc, Pair y, Pair u) {
+template <int NR>
+__device__ __forceinline__ void red2_add(const RedSpec& r, int ri, Acc2<NR>& acc, Pair y, Pair u) {
 #pragma unroll
-  for (int q = 0; q < kMaxRed; ++q) {
+  for (int q = 0; q < NR; ++q) {
     if (q == ri) {
       if (r.kind == RED_NORM2) {
         acc.v[q][0].x = fmaf(y.a.x, y.a.x, fmaf(y.a.y, y.a.y, acc.v[q][0].x));
@@ -120,14 +122,14 @@ __device__ __forceinline__ void red2_add(const RedSpec& r, int ri, Acc2& acc, Pa
 }
 
 // fixed-order CTA reduction; GP threads per row (GP column pairs), s = 2 * number of pairs
-template <int GP>
-__device__ __forceinline__ void cta_reduce2(const RedSet& rs, Acc2& acc, int s, float2* sm) {
+template <int GP, int NR>
+__device__ __forceinline__ void cta_reduce2(const RedSet& rs, Acc2<NR>& acc, int s, float2* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = blockDim.x >> 5;
   const int ns = rs.nslots;
   const int npairs = s / 2;
 #pragma unroll
-  for (int ri = 0; ri < kMaxRed; ++ri) {
+  for (int ri = 0; ri < NR; ++ri) {
     if (ri < rs.nred) {
       const RedSpec& r = rs.r[ri];
       if (r.kind == RED_CDOT || r.kind == RED_GRAMV) {
@@ -158,7 +160,10 @@ __device__ __forceinline__ void cta_reduce2(const RedSet& rs, Acc2& acc, int s, 
 // ---------------------------------------------------------------------------------------
 // SpMM (CSR, real-off-diagonal CSR or stencil) on column pairs
 // ---------------------------------------------------------------------------------------
-template <int GP>
+// STENCIL: the matrix-free stencil (a.nst > 0) or CSR; NR: accumulators for up to NR fused
+// reductions (rs.nred <= NR).  Separate instantiations keep the stencil's coefficients and
+// unused accumulators out of the registers of the CSR loop.
+template <int GP, bool STENCIL, int NR>
 __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArgs<float> a, RedSet rs, const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -176,19 +181,22 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
     ysc = make_float2((float)a.ay * d.x, (float)a.ay * d.y);
   }
   const float bz = (float)a.bz;
-  float2 stc = make_float2((float)a.sc.x, (float)a.sc.y), stm[3], stp[3];
+  float2 stc = make_float2(0.f, 0.f), stm[3], stp[3];
+  if constexpr (STENCIL) {
+    stc = make_float2((float)a.sc.x, (float)a.sc.y);
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    stm[q] = make_float2((float)a.sm[q].x, (float)a.sm[q].y);
-    stp[q] = make_float2((float)a.sp[q].x, (float)a.sp[q].y);
+    for (int q = 0; q < 3; ++q) {
+      stm[q] = make_float2((float)a.sm[q].x, (float)a.sm[q].y);
+      stp[q] = make_float2((float)a.sp[q].x, (float)a.sp[q].y);
+    }
   }
-  Acc2 acc;
+  Acc2<NR> acc;
 #pragma unroll
-  for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
+  for (int q = 0; q < NR; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
   const int64_t stride = (int64_t)gridDim.x * rows_per_cta;
   // CSR with s >= 8: the next rows' matrix entries and operands into L2 (measured: 6-9 % on the
   // fused product at s = 8-32; at s = 2 the row-pointer reads of the prefetching thread cost more)
-  const bool pf = a.nst == 0 && s >= 8;
+  const bool pf = !STENCIL && s >= 8;
   if (pf && threadIdx.x == 0) {
     for (int k = 0; k < kPrefetchAhead; ++k) {
       const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta + k * stride;
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
     const int64_t e = j * s + 2 * p;  // element index of column 2p in row j
     Pair y = pzero();
     if (act) {
-      if (a.nst > 0) {
+      if constexpr (STENCIL) {
         int64_t xc[3];
         int64_t rem = j;
 #pragma unroll
@@ -263,11 +271,30 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
 #pragma unroll
             for (int u = 0; u < 4; ++u) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
           }
-          for (; k < k1; ++k) {
-            const float v = a.offr[k];
-            const Pair x = gather(a.colidx[k]);
-            y.a = cfmareal<float>(v, x.a, y.a);
-            y.b = cfmareal<float>(v, x.b, y.b);
+          // the last 1-3 entries as one predicated batch: their loads are in flight together
+          // instead of one dependent index load and gather after another (with four
+          // accumulator slots this no longer fits the 64 registers: one entry at a time)
+          const int rem = (int)(k1 - k);
+          if constexpr (NR > 2) {
+            for (; k < k1; ++k) {
+              const float v = a.offr[k];
+              const Pair x = gather(a.colidx[k]);
+              y.a = cfmareal<float>(v, x.a, y.a);
+              y.b = cfmareal<float>(v, x.b, y.b);
+            }
+          } else if (rem > 0) {
+            int32_t col[3];
+            float v[3];
+            Pair x[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) x[u] = gather(col[u]);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
           }
         } else {
           for (; k + 4 <= k1; k += 4) {
@@ -281,11 +308,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
 #pragma unroll
             for (int u = 0; u < 4; ++u) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
           }
-          for (; k < k1; ++k) {
-            const float2 v = a.vals[k];
-            const Pair x = gather(a.colidx[k]);
-            y.a = cfma<float>(v, x.a, y.a);
-            y.b = cfma<float>(v, x.b, y.b);
+          const int rem = (int)(k1 - k);
+          if constexpr (NR > 2) {
+            for (; k < k1; ++k) {
+              const float2 v = a.vals[k];
+              const Pair x = gather(a.colidx[k]);
+              y.a = cfma<float>(v, x.a, y.a);
+              y.b = cfma<float>(v, x.b, y.b);
+            }
+          } else if (rem > 0) {
+            int32_t col[3];
+            float2 v[3];
+            Pair x[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) x[u] = gather(col[u]);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+              if (u < rem) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
           }
         }
       }
@@ -299,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
     }
     if (rs.nred > 0) {
 #pragma unroll
-      for (int ri = 0; ri < kMaxRed; ++ri) {
+      for (int ri = 0; ri < NR; ++ri) {
         if (ri < rs.nred) {
           const RedSpec& r = rs.r[ri];
           Pair u = pzero();
@@ -313,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
       }
     }
   }
-  if (rs.nred > 0) cta_reduce2<GP>(rs, acc, s, reinterpret_cast<float2*>(smem_raw));
+  if (rs.nred > 0) cta_reduce2<GP, NR>(rs, acc, s, reinterpret_cast<float2*>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -349,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
   __syncthreads();
   float2* red_sm = Dg + a.nmat * s;
   const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
-  Acc2 acc;
+  Acc2<> acc;
 #pragma unroll
   for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
   const int64_t stride = (int64_t)gridDim.x * rows_per_cta;
@@ -467,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
       }
     }
   }
-  if (rs.nred > 0) cta_reduce2<GP>(rs, acc, s, red_sm);
+  if (rs.nred > 0) cta_reduce2<GP, kMaxRed>(rs, acc, s, red_sm);
 }
 
 // Can this launch run on column pairs?  Even s, 16-byte aligned blocks, no s x s Gram,
