@@ -213,6 +213,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
     const bool act = rowok && p < npairs;
     const int64_t e = j * s + 2 * p;  // element index of column 2p in row j
     Pair y = pzero();
+    // CSR with at most two reductions: memory operands of the reductions loaded before the
+    // product (not after the store of Y), unless the operand is Y itself
+    constexpr bool kPre = !STENCIL && NR <= 2;
+    Pair upre[NR];
+    if constexpr (kPre) {
+#pragma unroll
+      for (int ri = 0; ri < NR; ++ri) {
+        upre[ri] = pzero();
+        if (ri < rs.nred && act && (rs.r[ri].kind == RED_TRACE || rs.r[ri].kind == RED_CDOT) &&
+            rs.r[ri].U != nullptr && rs.r[ri].U != static_cast<const void*>(a.Y))
+          upre[ri] = ld_pair(reinterpret_cast<const float2*>(rs.r[ri].U), e);
+      }
+    }
     if (act) {
       if constexpr (STENCIL) {
         int64_t xc[3];
@@ -347,7 +360,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
           const RedSpec& r = rs.r[ri];
           Pair u = pzero();
           if (r.kind == RED_TRACE || r.kind == RED_CDOT) {
-            if (act) u = (r.U != nullptr) ? ld_pair(reinterpret_cast<const float2*>(r.U), e) : y;
+            if (act) {
+              if (r.U == nullptr) u = y;
+              else if (kPre && r.U != static_cast<const void*>(a.Y)) u = upre[ri];
+              else u = ld_pair(reinterpret_cast<const float2*>(r.U), e);
+            }
           } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
             if (act) { u.a = reinterpret_cast<const float2*>(r.U)[j]; u.b = u.a; }
           }
