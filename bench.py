@@ -57,6 +57,9 @@ def parse_args():
                     help="time to 1e-8 per method on the 4D lattice (16^4 x 12, s = 12 point sources and 12 Gaussian)")
     ap.add_argument("--config4", action="store_true",
                     help="mixed precision vs FP64 on the 4D lattice (24^4 x 12, s = 32, eGl-BiCG to 1e-10)")
+    ap.add_argument("--spmm-rates", action="store_true",
+                    help="fused product + trace kernel rates only (complex64 and complex128) on 3D "
+                         "convection-diffusion (--grid, --s)")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=1)
     return ap.parse_args()
@@ -683,6 +686,47 @@ def config3(args):
     A.close()
 
 
+def spmm_rates(args):
+    """Rates of the product with a fused trace tr(U^H A V) (U a streamed n x s block), complex64
+    and complex128, on 3D convection-diffusion: CUDA events over 30 launches after 5 warm-up
+    launches.  Algorithmic bytes: the CSR arrays once (real off-diagonal storage: 4-byte index
+    and one real value per off-diagonal entry, complex diagonal, row pointers), V and U read,
+    Y written."""
+    import torch
+    import paper_1504_04395_gb300 as kr
+    torch.cuda.set_device(0)
+    op, rp, ci, v, _ = workload(args.grid, args.s)
+    A = kr.Operator(op.n, rp, ci, v, device=0)
+    n, s, nnz = op.n, args.s, len(ci)
+    real_off = A.info()["real_offdiag"]
+    hbm_peak, hbm_src = measured_peaks()
+    out = {"mode": "spmm_rates", "workload": "3D convection-diffusion %d^3 (n=%d, nnz=%d), s=%d" % (args.grid, n, nnz, s),
+           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
+    for dt, b, fn in ((torch.complex64, 8, kr.kr_op_apply_reduce_c64), (torch.complex128, 16, kr.kr_op_apply_reduce)):
+        g = torch.Generator(device="cuda").manual_seed(s)
+        V = torch.randn(n, s, dtype=dt, device="cuda", generator=g)
+        U = torch.randn(n, s, dtype=dt, device="cuda", generator=g)
+        Y = torch.empty_like(V)
+        for _ in range(5):
+            fn(A, V, U, kind="trace", Y=Y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(30):
+            fn(A, V, U, kind="trace", Y=Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 30
+        noff = nnz - n
+        mbytes = 8 * (n + 1) + (4 + b // 2) * noff + b * n if real_off else 8 * (n + 1) + (4 + b) * nnz
+        byts = mbytes + 3 * b * n * s
+        gbs = byts / ms / 1e6
+        out["c64" if b == 8 else "c128"] = {"ms": ms, "bytes": byts, "gbs": gbs, "hbm_frac": gbs / hbm_peak}
+        del V, U, Y
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
     if args.cpu_sample_worker:
@@ -699,6 +743,9 @@ def main():
         return
     if args.config4:
         config4(args)
+        return
+    if args.spmm_rates:
+        spmm_rates(args)
         return
     if args.impl == "reference":
         reference_arm(args)
