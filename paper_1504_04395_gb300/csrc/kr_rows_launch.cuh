@@ -1,6 +1,7 @@
 // Host launchers for the row kernels, instantiated once per element type.
 #pragma once
 
+#include <atomic>
 #include <unordered_map>
 
 #include "kr_internal.h"
@@ -14,11 +15,15 @@ namespace kr {
 constexpr int kMaxDynSmem = 200 * 1024;
 
 template <typename K>
-static void allow_smem(K kernel, bool& flag) {
-  if (!flag) {
-    KR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
-    flag = true;
-  }
+static void allow_smem(K kernel, std::atomic<uint64_t>& devices_done) {
+  // the attribute belongs to the current device: set once per device (bit d of devices_done),
+  // on every call for device ordinals beyond 63
+  int dev = 0;
+  KR_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t{1} << dev) : 0;
+  if (bit != 0 && (devices_done.load(std::memory_order_acquire) & bit)) return;
+  KR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem));
+  if (bit != 0) devices_done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 // Clamp a grid-stride grid to the CTAs that can be resident at once (at most kCtasPerSm per SM),
@@ -46,7 +51,7 @@ static int resident_grid(K kernel, size_t smem, int grid, std::unordered_map<siz
 
 template <typename T, int G, int NG>
 static void spmm_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
-  static bool attr = false;
+  static std::atomic<uint64_t> attr{0};
   allow_smem(spmm_kernel<T, G, NG>, attr);
   const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>) : 0;
   if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "spmm: too many reduction slots"};
@@ -95,13 +100,13 @@ static void lattice_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const 
   const int64_t tiles = (units + per_cta - 1) / per_cta;
   if ((int64_t)grid > tiles) grid = (int)(tiles > 0 ? tiles : 1);
   if (whole_site) {
-    static bool attr = false;
+    static std::atomic<uint64_t> attr{0};
     allow_smem(lattice_site_kernel<T, G, NG>, attr);
     thread_local std::unordered_map<size_t, int> occ;
     grid = resident_grid(lattice_site_kernel<T, G, NG>, smem, grid, occ);
     lattice_site_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
   } else {
-    static bool attr = false;
+    static std::atomic<uint64_t> attr{0};
     allow_smem(lattice_kernel<T, G, NG>, attr);
     thread_local std::unordered_map<size_t, int> occ;
     grid = resident_grid(lattice_kernel<T, G, NG>, smem, grid, occ);
@@ -237,7 +242,7 @@ int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* don
 
 template <typename T, int G, int NG>
 static void lin_go(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
-  static bool attr = false;
+  static std::atomic<uint64_t> attr{0};
   allow_smem(lincomb_kernel<T, G, NG>, attr);
   size_t smem = (size_t)a.nmat * a.s * a.s * sizeof(C2<T>);
   if (rs.nred > 0) smem += (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>);
