@@ -250,6 +250,23 @@ def test_block_bicg_petrov_galerkin(method):
         assert np.linalg.norm(Kh.conj().T @ Rk) < 1e-9 * np.linalg.norm(Kh) * np.linalg.norm(Rk)
 
 
+@pytest.mark.parametrize("method", ["bl_bicg", "bl_bicg_rq"])
+def test_block_bicg_petrov_galerkin_complex_offdiagonals(method):
+    """The same characterisation on a matrix with complex off-diagonal entries.  For the
+    convection-diffusion matrices (real off-diagonals, complex shift on the diagonal) the
+    Krylov spaces of A^T and A^H coincide (shift invariance), so only a matrix like this one
+    fixes that the shadow recurrence multiplies by A^H."""
+    from workloads.random_csr import random_csr
+    n, s = 40, 3
+    rp, ci, v = random_csr(n, max_row=5, seed=3, empty_frac=0.0)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    B = gaussian_block(n, s, 5)
+    Ad = A.toarray()
+    for k in (1, 2, 3):
+        r = oracle.solve(method, A, B, tol=0.0, maxit=k)
+        assert rel(r.X, _pg_iterate(Ad, B, B, k)) < 1e-9, (method, k)
+
+
 def test_global_bicg_petrov_galerkin():
     A, B = problem(N=6, s=3, shift=0.3j)
     K = kron_I(A, 3).toarray()
@@ -379,6 +396,20 @@ def test_block_qmr_quasi_minimal_random_shadow(k):
     Ad = A.toarray()
     r = oracle.solve("bl_qmr", A, B, tol=0.0, maxit=k, shadow=Rh0)
     assert rel(r.X, _qmr_bruteforce(Ad, B, Rh0, k)) < 1e-9
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_block_qmr_quasi_minimal_complex_offdiagonals(k):
+    """Brute-force quasi-minimal residual iterate on a matrix with complex off-diagonals (the
+    shadow side's A^H is only distinguishable from A^T on such a matrix)."""
+    from workloads.random_csr import random_csr
+    n = 30
+    rp, ci, v = random_csr(n, max_row=5, seed=4, empty_frac=0.0)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    B = gaussian_block(n, 2, 6)
+    Rh0 = gaussian_block(n, 2, 7)
+    r = oracle.solve("bl_qmr", A, B, tol=0.0, maxit=k, shadow=Rh0)
+    assert rel(r.X, _qmr_bruteforce(A.toarray(), B, Rh0, k)) < 1e-9
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
