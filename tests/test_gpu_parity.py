@@ -142,8 +142,11 @@ def test_s_edge_cases(kr, method, s):
     op.close()
 
 
-@pytest.mark.parametrize("method", ["egl_bicg", "bl_bicg", "gl_bicgstab", "bl_qmr", "egl_qmr"])
+@pytest.mark.parametrize("method", METHODS)
 def test_random_matrix_with_empty_rows(kr, method):
+    """Complex off-diagonal entries: the only kind of matrix on which a product with A^T in
+    place of A^H changes the iterates (for a complex shift of a real matrix both span the
+    same Krylov spaces)."""
     n = 777
     rp, ci, v = random_csr(n, max_row=6, seed=5, diag_shift=6.0 + 2.0j)
     B = gaussian_block(n, 3, seed=1)
