@@ -267,6 +267,34 @@ def test_block_bicg_petrov_galerkin_complex_offdiagonals(method):
         assert rel(r.X, _pg_iterate(Ad, B, B, k)) < 1e-9, (method, k)
 
 
+@pytest.mark.parametrize("method", ["bl_bicg", "bl_bicg_rq", "gl_bicg", "li_bicg"])
+def test_bicg_biorthogonality(method):
+    """Bi-orthogonality of the BiCG residuals (Sec. 2): Rh_j^H R_k = 0 for j != k (block),
+    tr(Rh_j^H R_k) = 0 (global), rh_{j,i}^H r_{k,i} = 0 per column (loop interchange).
+    BiCG treats its two sequences symmetrically, so the shadow residuals Rh_j are the
+    residuals Rh_0 - A^H Xh_j of the same method run on A^H Xh = Rh_0 with shadow R_0."""
+    A, B = problem(N=8, s=3, shift=0.3j)
+    Rh0 = gaussian_block(B.shape[0], 3, 21)
+    AH = oracle.adjoint(A)
+    K = 6
+    R = [B - A @ oracle.solve(method, A, B, tol=0.0, maxit=k, shadow=Rh0).X for k in range(K)]
+    Rh = [Rh0 - AH @ oracle.solve(method, AH, Rh0, tol=0.0, maxit=k, shadow=B).X for k in range(K)]
+
+    def coupling(U, V):
+        if method == "gl_bicg":
+            return abs(np.vdot(U, V)) / (np.linalg.norm(U) * np.linalg.norm(V))
+        if method == "li_bicg":
+            return max(abs(np.vdot(U[:, i], V[:, i])) / (np.linalg.norm(U[:, i]) * np.linalg.norm(V[:, i]))
+                       for i in range(U.shape[1]))
+        return np.linalg.norm(U.conj().T @ V) / (np.linalg.norm(U) * np.linalg.norm(V))
+
+    for j in range(K):
+        for k in range(K):
+            if j != k:
+                assert coupling(Rh[j], R[k]) < 1e-10, (j, k)
+    assert coupling(Rh[2], R[2]) > 1e-3  # the pairing itself is not degenerate
+
+
 def test_global_bicg_petrov_galerkin():
     A, B = problem(N=6, s=3, shift=0.3j)
     K = kron_I(A, 3).toarray()
