@@ -342,6 +342,26 @@ def test_rq_residual_norm_is_norm_of_C():
         assert r.history[-1] == pytest.approx(true, rel=1e-8)
 
 
+@pytest.mark.parametrize("pair", [("bl_bicg", "bl_bicg_rq"), ("bl_bicgstab", "bl_bicgstab_rq")])
+@pytest.mark.parametrize("eps", [1e-6, 1e-10])
+def test_rq_survives_nearly_dependent_columns(pair, eps):
+    """Sec. 4's motivation for the -rQ variants: when the columns of the block residual become
+    (nearly) linearly dependent, the s x s matrices of the block method are (nearly) singular
+    and it breaks down, while the variant that works with the QR factor Q of R converges.
+    Here two pairs of right-hand sides differ by eps."""
+    A, B = problem(N=16, pe=0.3, shift=0.3j, s=4, seed=2)
+    rng = np.random.default_rng(0)
+    B = B.copy()
+    B[:, 1] = B[:, 0] + eps * (rng.standard_normal(B.shape[0]) + 1j * rng.standard_normal(B.shape[0]))
+    B[:, 3] = B[:, 2] + eps * rng.standard_normal(B.shape[0])
+    plain = oracle.solve(pair[0], A, B, tol=1e-8, maxit=300)
+    rq = oracle.solve(pair[1], A, B, tol=1e-8, maxit=300)
+    assert plain.status == Status.BREAKDOWN
+    assert rq.status == Status.OK and rq.relres_true < 1e-7
+    Xd = np.linalg.solve(A.toarray(), B)
+    assert rel(rq.X, Xd) < 1e-5
+
+
 def test_rq_invariant_under_qr_phase(monkeypatch):
     """X does not depend on the phases of the diagonal of the QR factors."""
     A, B = problem(N=10, s=3, shift=0.4j)
