@@ -36,6 +36,7 @@ class Result:
     matvecs: int
     history: list = field(default_factory=list)  # ||R_k||/||R_0|| for k = 0..iters
     relres_true: float = float("nan")  # ||B - A X||_F / ||R_0||_F at exit
+    breakdown_iter: int = 0  # BREAKDOWN: the iteration (iters + 1) that could not be completed; else 0
 
 
 class _Monitor:
@@ -256,6 +257,17 @@ def _omega(T, S):
     return ts / tt
 
 
+def _omega_weighted(Tp, Sp, C):
+    """omega of Bl-BiCGStab-rQ: tr(T'^H S' C C^H) / tr(T'^H T' C C^H), which is omega = tr(T^H S) /
+    tr(T^H T) of Bl-BiCGStab for S = S' C, T = T' C; 0 if the denominator vanishes."""
+    CC = C @ C.conj().T
+    num = np.trace(gram(Tp, Sp) @ CC)
+    den = np.trace(gram(Tp, Tp) @ CC)
+    if not (np.isfinite(num) and np.isfinite(den)):
+        raise FloatingPointError("non-finite omega")
+    return 0.0 if den == 0 else num / den
+
+
 def gl_bicgstab(A, AH, B, X0, Rt0, mon):
     """Gl-BiCGStab: van der Vorst's BiCGStab for (I (x) A) x = b with <X, Y> = tr(Y^H X).
 
@@ -387,12 +399,7 @@ def bl_bicgstab_rq(A, AH, B, X0, Rt0, mon):
         alpha = lu_solve(M, gram(Rt, Q))
         Sp = Q - W @ alpha
         Tp = spmm(A, Sp)
-        CC = C @ C.conj().T
-        num = np.trace(gram(Tp, Sp) @ CC)
-        den = np.trace(gram(Tp, Tp) @ CC)
-        if not (np.isfinite(num) and np.isfinite(den)):
-            raise FloatingPointError("non-finite omega")
-        omega = 0.0 if den == 0 else num / den
+        omega = _omega_weighted(Tp, Sp, C)
         X = X + (V @ alpha + omega * Sp) @ C
         Q_new, Sig = thin_qr(Sp - omega * Tp)
         C = Sig @ C
@@ -747,20 +754,44 @@ METHODS = {
 }
 
 
-def solve(method, A, B, X0=None, tol=1e-8, maxit=500, shadow=None, AH=None):
+def solve(method, A, B, X0=None, tol=1e-8, maxit=500, shadow=None, AH=None, orthonormalize_B=False):
     """Run ``method`` on A X = B; returns a Result.
 
     ``shadow``: initial shadow residual block (n x s) for the block/global
     methods, or the single shadow vector (n) for the economic methods; None
     selects the paper's defaults (R_0, or the mean of R_0's columns).
+
+    ``orthonormalize_B``: the set-up of Sec. 5, in which the right-hand sides are
+    replaced by the orthonormal factor Q of their thin QR decomposition.  With an
+    initial guess: R_0 = B - A X_0 = Q S, the method solves A Y = Q from Y = 0, and
+    X = X_0 + Y S.  The history and the stopping test refer to the system with Q,
+    relres_true to A X = B.
     """
-    fn = METHODS[method]
     B = np.asarray(B, dtype=np.complex128)
     if B.ndim == 1:
         B = B[:, None]
     X0 = np.zeros_like(B) if X0 is None else np.asarray(X0, dtype=np.complex128).copy()
     if AH is None:
         AH = adjoint(A)
+    if orthonormalize_B:
+        R0 = B - spmm(A, X0)
+        nrm0 = frob(R0)
+        if nrm0 == 0.0 or not np.isfinite(nrm0):
+            st = Status.OK if nrm0 == 0.0 else Status.NAN
+            return Result(X=X0, status=st, iters=0, matvecs=0, history=[1.0], relres_true=nrm0)
+        Q, S = thin_qr(R0)
+        d = np.abs(np.diag(S))
+        if np.any(d <= 64.0 * np.finfo(float).eps * np.linalg.norm(S)):  # numerically rank deficient
+            return Result(X=X0, status=Status.BREAKDOWN, iters=0, matvecs=0, history=[1.0], relres_true=1.0,
+                          breakdown_iter=1)
+        r = solve(method, A, Q, None, tol=tol, maxit=maxit, shadow=shadow, AH=AH)
+        X = X0 + r.X @ S
+        r.X = X
+        r.relres_true = float(frob(B - spmm(A, X)) / nrm0)
+        if r.status == Status.MAXIT and r.relres_true > 1.0:
+            r.status = Status.DIVERGED
+        return r
+    fn = METHODS[method]
     mon = _Monitor(tol, maxit)
     mon.X = X0
     with np.errstate(all="ignore"):
@@ -781,4 +812,4 @@ def solve(method, A, B, X0=None, tol=1e-8, maxit=500, shadow=None, AH=None):
     if not np.isfinite(rel) and status != Status.BREAKDOWN:
         status = Status.NAN
     return Result(X=X, status=status, iters=mon.iters, matvecs=mon.matvecs, history=mon.history,
-                  relres_true=float(rel))
+                  relres_true=float(rel), breakdown_iter=mon.iters + 1 if status == Status.BREAKDOWN else 0)

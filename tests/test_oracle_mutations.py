@@ -29,6 +29,21 @@ def _omega_swapped(T, S):
     return M.__dict__["_omega_orig"](S, T)
 
 
+class _BetaSolveTransposed:
+    """lu_solve with its matrix transposed whenever it receives the same matrix object twice in a
+    row.  Bl-BiCGStab and Bl-BiCGStab-rQ are the only methods whose beta solve reuses the alpha
+    solve's matrix (Rt^H V, resp. Rt^H W), so this plants a transposed beta solve in both
+    variants alike: a reading error the two would share, invisible at s = 1."""
+
+    def __init__(self):
+        self.last = None
+
+    def __call__(self, Mx, N):
+        same = Mx is self.last
+        self.last = Mx
+        return _lu_solve(np.asarray(Mx).T if same else Mx, N)
+
+
 def _givens_sign_flipped(a, b):
     """The complex Givens rotation with the sign of its off-diagonal entry flipped, so that it
     no longer annihilates b."""
@@ -60,6 +75,14 @@ def _ilu0_conj_pivots(A):
     return L, (U - sp.diags(d) + sp.diags(np.conj(d))).tocsr()
 
 
+def _stab_pin(method):
+    """The Omega-polynomial pin of Bl-BiCGStab on the complex matrix, with its own monkeypatch."""
+    def run():
+        with pytest.MonkeyPatch.context() as mp:
+            pins.test_block_stab_is_omega_polynomial_times_block_bicg(method, "complex", mp)
+    return run
+
+
 # name -> (module, attribute, replacement, pins that must not all pass)
 MUTATIONS = {
     # Sec. 2, Algorithm 3: the s x s matrices are Ph^H Q and Rh^H R
@@ -89,6 +112,11 @@ MUTATIONS = {
     "omega with swapped operands": (
         M, "_omega", _omega_swapped,
         [pins.test_global_bicgstab_is_kron_bicgstab, lambda: pins.test_s1_reduces_to_bicgstab("bl_bicgstab")]),
+    # Bl-BiCGStab at s > 1 (Sec. 2, El Guennouni-Jbilou-Sadok): (Rt^H V) beta = -Rt^H T, shared by
+    # the -rQ variant; caught by the Omega-polynomial pin without the s = 1 or rQ-equality pins
+    "beta solve transposed in both block BiCGStab variants": (
+        M, "lu_solve", _BetaSolveTransposed(),
+        [_stab_pin("bl_bicgstab"), _stab_pin("bl_bicgstab_rq")]),
     # the shadow recurrences multiply by A^H, not A^T (distinguishable only with complex
     # off-diagonal entries: for a complex shift of a real matrix both give the same Krylov spaces)
     "adjoint without conjugate": (

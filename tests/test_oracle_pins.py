@@ -397,6 +397,60 @@ def test_block_stab_krylov_space():
         assert np.linalg.norm(r.X - Qk @ (Qk.conj().T @ r.X)) < 1e-10 * np.linalg.norm(r.X)
 
 
+def _stab_problem(kind):
+    if kind == "convdiff":
+        return problem(N=6, s=3, shift=0.3j)
+    from workloads.random_csr import random_csr
+    n = 40
+    rp, ci, v = random_csr(n, max_row=5, seed=3, empty_frac=0.0)
+    return oracle.csr_matrix_from_arrays(n, rp, ci, v), gaussian_block(n, 3, 5)
+
+
+@pytest.mark.parametrize("method", ["bl_bicgstab", "bl_bicgstab_rq"])
+@pytest.mark.parametrize("kind", ["convdiff", "complex"])
+def test_block_stab_is_omega_polynomial_times_block_bicg(method, kind, monkeypatch):
+    """Bl-BiCGStab of El Guennouni, Jbilou and Sadok (Sec. 2; the -rQ variant of Sec. 4 is the same
+    method in exact arithmetic) at s > 1, from its defining property: after k steps
+    R_k = Omega_k(A) R_k^BlBiCG with the scalar polynomial Omega_k(t) = prod_j (1 - omega_j t), where
+    R_k^BlBiCG is the block-BiCG residual for the shadow block Rt_0 = R_0 (fixed here by brute-force
+    Petrov-Galerkin, R_k^BlBiCG orthogonal to K_k(A^H, Rt_0)), and omega_k is the global
+    steepest-descent step, the minimiser of ||(I - omega A) S_k||_F over omega for
+    S_k = Omega_{k-1}(A) R_k^BlBiCG.  The omegas are recorded from the oracle's run; Omega_k(A)^{-1}
+    R_k is formed by dense solves.  On the matrix with complex off-diagonal entries a transposed or
+    unconjugated s x s solve anywhere in the recurrences breaks the identity at k >= 2."""
+    import oracle.methods as M
+    A, B = _stab_problem(kind)
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    I = np.eye(n)
+    omegas = []
+    name = "_omega" if method == "bl_bicgstab" else "_omega_weighted"
+    orig = getattr(M, name)
+
+    def recording(*args):
+        w = orig(*args)
+        omegas.append(complex(w))
+        return w
+
+    monkeypatch.setattr(M, name, recording)
+    for k in (1, 2, 3, 4):
+        omegas.clear()
+        r = oracle.solve(method, A, B, tol=0.0, maxit=k)
+        assert r.iters == k and len(omegas) == k
+        Rk = B - Ad @ r.X
+        R_bl = B - Ad @ _pg_iterate(Ad, B, B, k)
+        Z = Rk
+        for w in omegas:
+            Z = np.linalg.solve(I - w * Ad, Z)
+        assert rel(Z, R_bl) < 1e-9, (method, kind, k, rel(Z, R_bl))
+        S = R_bl
+        for w in omegas[:-1]:
+            S = (I - w * Ad) @ S
+        T = Ad @ S
+        w_def = np.vdot(T, S) / np.vdot(T, T)  # argmin_w ||S - w T||_F
+        assert abs(omegas[-1] - w_def) <= 1e-9 * abs(w_def), (method, kind, k)
+
+
 # ------------------------------------------------------------------------------------------
 # QMR: brute-force quasi-minimal residual from a dense bi-orthogonal basis (Sec. 2)
 # ------------------------------------------------------------------------------------------
@@ -541,3 +595,50 @@ def test_adjoint_identity():
     AH = oracle.adjoint(A)
     x, y = B[:, 0], B[:, 1]
     assert np.vdot(y, A @ x) == pytest.approx(np.vdot(AH @ y, x), rel=1e-13)
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 5 set-up: orthonormalised right-hand sides (B replaced by Q of B = Q S)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", ["egl_bicg", "gl_bicg", "bl_bicg", "bl_bicg_rq", "bl_bicgstab", "gl_qmr"])
+def test_orthonormalized_rhs_gives_the_same_solution(method):
+    """With orthonormalize_B the method runs on A Y = Q (B - A X_0 = Q S) and X = X_0 + Y S is
+    returned: the same solution of A X = B, here against dense LU, from X_0 = 0 and from a
+    non-zero X_0.  For the block methods the iterates themselves coincide with those of the plain
+    run (the block Krylov spaces of R_0 and R_0 S^{-1} are equal and Bl-BiCG's Petrov-Galerkin
+    conditions do not depend on the basis), which fixes that X = X_0 + Y S and not Y S^{-1}."""
+    A, B = problem(N=8, s=3, shift=0.4j)
+    Xd = np.linalg.solve(A.toarray(), B)
+    X0 = 0.1 * gaussian_block(B.shape[0], 3, 7)
+    for x0 in (None, X0):
+        r = oracle.solve(method, A, B, X0=x0, tol=1e-12, maxit=400, orthonormalize_B=True)
+        assert r.status == Status.OK, (method, r.status)
+        assert rel(r.X, Xd) < 1e-9
+        assert r.relres_true < 1e-10
+    if method in ("bl_bicg", "bl_bicg_rq"):
+        for k in (1, 2, 3):
+            a = oracle.solve(method, A, B, tol=0.0, maxit=k, orthonormalize_B=True)
+            b = oracle.solve(method, A, B, tol=0.0, maxit=k, shadow=None)
+            # shadow: the plain run's default shadow is R_0, the orthonormalised run's is Q;
+            # both span the same block Krylov spaces, so the Petrov-Galerkin iterate is the same
+            assert rel(a.X, b.X) < 1e-9, (method, k)
+
+
+def test_orthonormalized_rhs_rank_deficient_is_breakdown():
+    A, B = problem(N=6, s=3, shift=0.4j)
+    B = B.copy()
+    B[:, 2] = B[:, 0]
+    r = oracle.solve("gl_bicg", A, B, tol=1e-10, maxit=50, orthonormalize_B=True)
+    assert r.status == Status.BREAKDOWN and r.breakdown_iter == 1 and r.iters == 0
+
+
+def test_breakdown_iter_is_the_failing_iteration():
+    """Duplicate right-hand sides make Bl-BiCG's first s x s matrix singular (Sec. 2)."""
+    A, B = problem(N=6, s=3, shift=0.4j)
+    B = B.copy()
+    B[:, 2] = B[:, 1]
+    r = oracle.solve("bl_bicg", A, B, tol=1e-10, maxit=50)
+    assert r.status == Status.BREAKDOWN and r.breakdown_iter == r.iters + 1 == 1
+    ok = oracle.solve("gl_bicg", A, B, tol=1e-10, maxit=200)
+    assert ok.status == Status.OK and ok.breakdown_iter == 0
