@@ -102,6 +102,17 @@ typedef struct {
                              Two iterations are captured once and replayed until convergence; the
                              results are bitwise those of the eager launches.  Off while the launch
                              profile times kernels. */
+  int32_t orthonormalize_B; /* 1: the set-up of Sec. 5, right-hand sides replaced by the orthonormal
+                             factor of a thin QR: R_0 = B - A X_0 = Q S (Q^H Q = I, S upper triangular
+                             with real positive diagonal), the method solves A Y = Q from Y = 0 and
+                             X = X_0 + Y S is returned.  tol, history and relres_recursive refer to
+                             the system with Q; relres_true to the caller's system.  KR_BREAKDOWN
+                             (breakdown_iter 1) when R_0 is numerically rank deficient.  Not with a
+                             preconditioner (KR_UNSUPPORTED).  0 (default): B as given. */
+  int32_t deterministic;  /* 0 or 1.  Every reduction of the library sums its per-CTA partial sums in
+                             a fixed order over a grid fixed by (n, s, device), so results are bitwise
+                             reproducible on a given device with either value; the field records the
+                             caller's requirement and rejects other values (KR_BAD_ARG). */
   int32_t reserved;
 } kr_options;
 
@@ -114,10 +125,13 @@ typedef struct {
   int32_t outer_iters;      /* KR_FP32_REFINE: defect-correction steps */
   int32_t fp64_iters;       /* KR_FP32_REFINE: iterations of the FP64 solve that finishes the job when a
                                complex64 inner solve failed to reduce the FP64 residual (0: none) */
-  int32_t reserved;
+  int32_t breakdown_iter;   /* status KR_BREAKDOWN: the iteration (1-based; iters + 1) whose scalar
+                               denominator vanished or whose s x s matrix was singular (Secs. 2, 4);
+                               X and the residuals are those after iters iterations.  0 otherwise */
 } kr_info;
 
-/* Fill *opt with defaults: tol 1e-8, maxit 500, FP64, default shadow, check_every 8. */
+/* Fill *opt with defaults: tol 1e-8, maxit 500, FP64, default shadow, check_every 8,
+ * B as given (orthonormalize_B 0), deterministic 1. */
 KR_API void kr_options_default(kr_options* opt);
 
 /* Build an operator from a CSR matrix (Sec. 1: A sparse, used only through
@@ -133,6 +147,15 @@ KR_API void kr_options_default(kr_options* opt);
  * malformed CSR (checked on the host), KR_OOM when device memory runs out. */
 KR_API kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                            const double* vals, int32_t device, kr_op* out);
+
+/* kr_op_create_csr for arrays that may live on the device: with on_device != 0, rowptr,
+ * colidx and vals are device pointers of the device that `stream` belongs to (the current
+ * device when stream is NULL), copied on `stream` (the call waits for the copies); with
+ * on_device == 0 they are host pointers and the operator is built on the current device.
+ * The caller keeps ownership.  Validation, the explicit A^H and the storage choice are those
+ * of kr_op_create_csr (made on the host from the copied arrays); errors as there. */
+KR_API kr_status kr_op_create_csr_async(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                                        const double* vals, int32_t on_device, void* stream, kr_op* out);
 
 /* Matrix-free operator of a (2d+1)-point stencil on a d-dimensional grid (d = 1, 2, 3)
  * with Dirichlet boundaries (the convection-diffusion discretisations of Sec. 5,
@@ -245,10 +268,16 @@ KR_API kr_status kr_block_reduce_c64(int64_t n, int32_t s, const float* U, const
  * Arguments and result as kr_block_reduce; out is caller-owned device memory.
  * Limit: 1 <= s <= 16, otherwise KR_UNSUPPORTED before any GPU work.  The
  * scratch (per-CTA partial sums) is a 1 MiB statically sized device array held
- * by every GPU that loads the library until process exit.  The first call on a
- * device looks up that array's device address once; make it before any stream
- * capture.  All calls share the array (each fully overwrites what it reads, so
- * nothing needs clearing); calls whose GPU work overlaps race on it. */
+ * by every GPU that loads the library until process exit.  The call runs on the
+ * device that holds Y (made current for the call, the previous device restored);
+ * U, out and a non-null stream on another device give KR_BAD_ARG.  The array's
+ * device address is looked up on every call made outside a stream capture; a call
+ * made while its stream is being captured reuses the address of the last
+ * uncaptured call on that device, so call once on each device before capturing.
+ * The grid is capped at 256 CTAs, so for large n the result agrees with
+ * kr_block_reduce to rounding, not bitwise.  All calls share the array (each
+ * fully overwrites what it reads, so nothing needs clearing); calls whose GPU work
+ * overlaps race on it. */
 KR_API kr_status kr_block_reduce_noalloc(int64_t n, int32_t s, const double* U, const double* Y, int32_t kind,
                                          double* out, void* stream);
 

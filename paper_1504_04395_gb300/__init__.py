@@ -48,6 +48,8 @@ class KrOptions(ctypes.Structure):
         ("history", ctypes.POINTER(ctypes.c_double)),
         ("time_limit_s", ctypes.c_double),
         ("graphs", ctypes.c_int32),
+        ("orthonormalize_B", ctypes.c_int32),
+        ("deterministic", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
     ]
 
@@ -61,7 +63,7 @@ class KrInfo(ctypes.Structure):
         ("status", ctypes.c_int32),
         ("outer_iters", ctypes.c_int32),
         ("fp64_iters", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("breakdown_iter", ctypes.c_int32),
     ]
 
 
@@ -83,6 +85,7 @@ _I64 = ctypes.c_int64
 SIGNATURES = {
     "kr_options_default": (None, [ctypes.POINTER(KrOptions)]),
     "kr_op_create_csr": (_I32, [_I64, _I64, _P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "kr_op_create_csr_async": (_I32, [_I64, _I64, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)]),
     "kr_op_destroy": (_I32, [_P]),
     "kr_op_create_stencil": (_I32, [_I32, _P, _P, _I32, ctypes.POINTER(_P)]),
     "kr_op_create_lattice4d": (_I32, [_P, _P, ctypes.c_double, _P, _P, _I32, ctypes.POINTER(_P)]),
@@ -260,6 +263,34 @@ class Operator:
                                       vals.ctypes.data, self.device, ctypes.byref(h)))
         self._h = h
 
+    @classmethod
+    def from_tensors(cls, rowptr, colidx, vals, stream=None):
+        """Operator from CSR arrays held in torch tensors (kr_op_create_csr_async): int64 rowptr,
+        int32 colidx and complex128 vals, all on one CUDA device (copied on `stream`) or all on the
+        host."""
+        torch = _torch()
+        n = int(rowptr.shape[0]) - 1
+        nnz = int(colidx.shape[0])
+        on_dev = rowptr.is_cuda
+        if {t.is_cuda for t in (rowptr, colidx, vals)} != {on_dev}:
+            raise ValueError("rowptr, colidx and vals must all be on the device or all on the host")
+        for t, name, dt in ((rowptr, "rowptr", torch.int64), (colidx, "colidx", torch.int32),
+                            (vals, "vals", torch.complex128)):
+            if t.dtype != dt or not t.is_contiguous():
+                raise TypeError("%s must be a contiguous %s tensor" % (name, dt))
+        if vals.shape[0] != nnz:
+            raise ValueError("vals and colidx differ in length")
+        self = cls.__new__(cls)
+        self.n, self.nnz = n, nnz
+        h = ctypes.c_void_p()
+        st = _stream(stream) if on_dev else ctypes.c_void_p(0)
+        _check(lib().kr_op_create_csr_async(n, nnz, ctypes.c_void_p(rowptr.data_ptr()),
+                                            ctypes.c_void_p(colidx.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                            int(on_dev), st, ctypes.byref(h)))
+        self._h = h
+        self.device = rowptr.device.index if on_dev else torch.cuda.current_device()
+        return self
+
     @property
     def handle(self):
         return self._h
@@ -381,14 +412,28 @@ def kr_block_reduce_noalloc(U, Y, out, kind="gram", stream=None):
     """kr_block_reduce into a caller-provided `out` with no device allocation by the library.
 
     For callers whose device memory is owned by their own allocator or who cannot
-    afford an allocation in the call; s <= 16; see include/kr.h for the limits.
+    afford an allocation in the call; s <= 16.  `out` must be a complex128 device
+    tensor of shape (s, s) for "gram" and (1,) otherwise; U has shape (n, s) for
+    "gram" / "trace" and (n,) for "sumv" (ignored for "norm2"); U, Y, out on one device.
     """
     torch = _torch()
     n, s = Y.shape
     k = RED[kind] if isinstance(kind, str) else int(kind)
-    uptr = ctypes.c_void_p(0) if (U is None) else _dev_ptr(U, "U", torch.complex128)
-    _check(lib().kr_block_reduce_noalloc(n, s, uptr, _dev_ptr(Y, "Y", torch.complex128), k, _dev_ptr(out, "out"),
-                                         _stream(stream)))
+    if k not in RED.values():
+        raise ValueError("unknown reduction kind %r" % (kind,))
+    yptr = _dev_ptr(Y, "Y", torch.complex128, (n, s))
+    optr = _dev_ptr(out, "out", torch.complex128, (s, s) if k == RED["gram"] else (1,))
+    devices = {Y.device, out.device}
+    if k == RED["norm2"] or U is None:
+        if k != RED["norm2"]:
+            raise ValueError("U is required for reduction %r" % (kind,))
+        uptr = ctypes.c_void_p(0)
+    else:
+        uptr = _dev_ptr(U, "U", torch.complex128, (n,) if k == RED["sumv"] else (n, s))
+        devices.add(U.device)
+    if len(devices) != 1:
+        raise ValueError("U, Y and out must be on one device, got %s" % sorted(str(d) for d in devices))
+    _check(lib().kr_block_reduce_noalloc(n, s, uptr, yptr, k, optr, _stream(stream)))
     return out
 
 
@@ -413,6 +458,7 @@ class SolveInfo:
     outer_iters: int
     history: list
     fp64_iters: int = 0
+    breakdown_iter: int = 0
 
     @property
     def converged(self):
@@ -420,7 +466,7 @@ class SolveInfo:
 
 
 def _options(tol, maxit, precision, inner_tol, max_outer, shadow, shadow_mode, check_every, host_buffers,
-             history, time_limit_s, graphs=0):
+             history, time_limit_s, graphs=0, orthonormalize_B=False):
     o = KrOptions()
     lib().kr_options_default(ctypes.byref(o))
     o.tol = float(tol)
@@ -435,11 +481,12 @@ def _options(tol, maxit, precision, inner_tol, max_outer, shadow, shadow_mode, c
     o.history = history
     o.time_limit_s = float(time_limit_s)
     o.graphs = int(graphs)
+    o.orthonormalize_B = int(bool(orthonormalize_B))
     return o
 
 
 def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, shadow, shadow_conj, check_every,
-           stream, time_limit_s, graphs=0):
+           stream, time_limit_s, graphs=0, orthonormalize_B=False):
     torch = _torch()
     n, s = B.shape
     host = not B.is_cuda
@@ -462,7 +509,7 @@ def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, sh
     elif shadow_conj:
         mode = 1
     o = _options(tol, maxit, precision, inner_tol, max_outer, sptr, mode, check_every, host, hist, time_limit_s,
-                 GRAPHS[graphs] if isinstance(graphs, str) else int(graphs))
+                 GRAPHS[graphs] if isinstance(graphs, str) else int(graphs), orthonormalize_B)
     info = KrInfo()
     st = fn(op.handle, method_id(method), s, bptr, xptr, ctypes.byref(o), _stream(stream), ctypes.byref(info))
     _check(st, allow_iteration_status=True)
@@ -470,26 +517,28 @@ def _solve(fn, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, sh
     si = SolveInfo(status=STATUS[info.status], iters=info.iters, matvecs=info.matvecs,
                    relres_recursive=info.relres_recursive, relres_true=info.relres_true,
                    outer_iters=info.outer_iters, history=[hist[i] for i in range(min(nh, maxit + 1))],
-                   fp64_iters=info.fp64_iters)
+                   fp64_iters=info.fp64_iters, breakdown_iter=info.breakdown_iter)
     return X, si
 
 
 def kr_solve(op: Operator, method, B, X=None, tol=1e-8, maxit=500, precision=FP64, inner_tol=1e-4, max_outer=30,
-             shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0, graphs="auto"):
+             shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0, graphs="auto",
+             orthonormalize_B=False):
     """Solve A X = B (B: n x s complex128, CUDA or CPU tensor; X holds X_0, default 0).
 
     graphs: "auto" (CUDA-graph replay of the iterations for small problems), "on" or "off".
+    orthonormalize_B: solve with the orthonormal factor Q of B - A X_0 = Q S (Sec. 5) and map back.
     """
     return _solve(lib().kr_solve, op, method, B, X, tol, maxit, precision, inner_tol, max_outer, shadow,
-                  shadow_conj, check_every, stream, time_limit_s, graphs)
+                  shadow_conj, check_every, stream, time_limit_s, graphs, orthonormalize_B)
 
 
 def kr_adjoint_solve(op: Operator, method, G, Lam=None, tol=1e-8, maxit=500, precision=FP64, inner_tol=1e-4,
                      max_outer=30, shadow=None, shadow_conj=False, check_every=8, stream=None, time_limit_s=0.0,
-                     graphs="auto"):
+                     graphs="auto", orthonormalize_B=False):
     """Solve A^H Lambda = G with the same simultaneous methods."""
     return _solve(lib().kr_adjoint_solve, op, method, G, Lam, tol, maxit, precision, inner_tol, max_outer, shadow,
-                  shadow_conj, check_every, stream, time_limit_s, graphs)
+                  shadow_conj, check_every, stream, time_limit_s, graphs, orthonormalize_B)
 
 
 def kr_grad_values(op: Operator, Lam, X, stream=None):

@@ -1,4 +1,5 @@
 // extern "C" boundary of the library (declared in include/kr.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -165,6 +166,7 @@ void kr_options_default(kr_options* opt) {
   opt->max_outer = 30;
   opt->shadow_mode = KR_SHADOW_DEFAULT;
   opt->check_every = 8;
+  opt->deterministic = 1;
 }
 
 const char* kr_last_error(void) { return get_error(); }
@@ -211,6 +213,55 @@ kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const 
   KR_CUDA(cudaMallocHost(&op.pinned, 4096));
   *out = h.release();
   return KR_OK;
+  KR_API_END
+}
+
+kr_status kr_op_create_csr_async(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
+                                 const double* vals, int32_t on_device, void* stream, kr_op* out) {
+  if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }
+  *out = nullptr;
+  if (n <= 0 || nnz < 0 || !rowptr || (nnz > 0 && (!colidx || !vals))) {
+    set_error("invalid CSR sizes or NULL arrays");
+    return KR_BAD_ARG;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  if (st != nullptr) {
+    if (cudaStreamGetDevice(st, &dev) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cannot determine the device of the stream");
+      return KR_BAD_ARG;
+    }
+  } else if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return KR_CUDA_ERROR;
+  }
+  if (!on_device) return kr_op_create_csr(n, nnz, rowptr, colidx, vals, dev, out);
+  KR_API_BEGIN
+  KR_CUDA(cudaSetDevice(dev));
+  // staged through pinned host memory on the caller's stream; the host builds A^H and checks
+  // the arrays exactly as for host input
+  int64_t* hr = nullptr;
+  int32_t* hc = nullptr;
+  double* hv = nullptr;
+  struct PinGuard {
+    void* p[3] = {nullptr, nullptr, nullptr};
+    ~PinGuard() { for (void* q : p) if (q) cudaFreeHost(q); }
+  } pg;
+  KR_CUDA(cudaMallocHost(&hr, sizeof(int64_t) * (n + 1)));
+  pg.p[0] = hr;
+  KR_CUDA(cudaMallocHost(&hc, sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+  pg.p[1] = hc;
+  KR_CUDA(cudaMallocHost(&hv, sizeof(double2) * std::max<int64_t>(nnz, 1)));
+  pg.p[2] = hv;
+  KR_CUDA(cudaMemcpyAsync(hr, rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, st));
+  if (nnz > 0) {
+    KR_CUDA(cudaMemcpyAsync(hc, colidx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st));
+    KR_CUDA(cudaMemcpyAsync(hv, vals, sizeof(double2) * nnz, cudaMemcpyDeviceToHost, st));
+  }
+  KR_CUDA(cudaStreamSynchronize(st));
+  return kr_op_create_csr(n, nnz, hr, hc, hv, dev, out);
   KR_API_END
 }
 
@@ -574,6 +625,12 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
     set_error("the ILU(0) preconditioner is supported for kr_solve in FP64");
     return KR_UNSUPPORTED;
   }
+  if (opt.orthonormalize_B != 0 && opt.orthonormalize_B != 1) { set_error("orthonormalize_B must be 0 or 1"); return KR_BAD_ARG; }
+  if (opt.deterministic != 0 && opt.deterministic != 1) { set_error("deterministic must be 0 or 1"); return KR_BAD_ARG; }
+  if (opt.orthonormalize_B && op->op.ilu.on) {
+    set_error("orthonormalize_B is not supported together with a preconditioner");
+    return KR_UNSUPPORTED;
+  }
   KR_API_BEGIN
   Operator& o = op->op;
   KR_CUDA(cudaSetDevice(o.device));
@@ -605,7 +662,33 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
   // triangular solves makes those iterations launch-bound)
   in.graphs = (opt.graphs == 1 || (opt.graphs == 0 && ((int64_t)o.n * s <= ((int64_t)1 << 22) || o.ilu.on))) ? 1 : 0;
   kr_info inf{};
-  if (opt.precision == KR_FP64 && o.ilu.on) {
+  // orthonormalised right-hand sides (Sec. 5): R_0 = B - A X_0 = Q S, solve A Y = Q from Y = 0,
+  // then X = X_0 + Y S; the iteration and its history are those of the system with Q
+  const double* uB = dB;
+  double* uX = dX;
+  double ortho_res0 = 0.0;
+  bool ortho_skip = false;
+  if (opt.orthonormalize_B) {
+    void *Qp = nullptr, *Yp = nullptr;
+    ortho_res0 = orthonormal_rhs(o, s, dB, dX, &Qp, &Yp, st, adjoint);
+    if (ortho_res0 < 0.0) {
+      inf.status = KR_BREAKDOWN;
+      inf.relres_recursive = inf.relres_true = 1.0;
+      if (opt.history) opt.history[0] = 1.0;
+      set_error("orthonormalize_B: the initial residual block is numerically rank deficient");
+      ortho_skip = true;
+    } else if (!(ortho_res0 > 0.0)) {  // X_0 solves the system (0) or the residual is not finite
+      inf.status = ortho_res0 == 0.0 ? KR_OK : KR_NAN;
+      inf.relres_true = inf.relres_recursive = ortho_res0 == 0.0 ? 0.0 : ortho_res0;
+      if (opt.history) opt.history[0] = 1.0;
+      ortho_skip = true;
+    }
+    dB = reinterpret_cast<const double*>(Qp);
+    dX = reinterpret_cast<double*>(Yp);
+  }
+  if (ortho_skip) {
+    // nothing to iterate
+  } else if (opt.precision == KR_FP64 && o.ilu.on) {
     // right preconditioning: A M^{-1} Y = B - A X0 from Y = 0, then X = X0 + M^{-1} Y
     Workspace& rw = get_workspace(o, s, 24, 4, 0, 1);
     void *R0 = rw.blocks[0], *Yb = rw.blocks[1], *Tb = rw.blocks[2];
@@ -717,8 +800,14 @@ static kr_status solve_impl(kr_op op, int32_t method, int32_t s, const double* B
     inf.relres_recursive = res0 > 0 ? res / res0 : res;
     inf.relres_true = inf.relres_recursive;
   }
+  if (opt.orthonormalize_B && !ortho_skip) {
+    add_back_rhs_factor(o, s, uX, st);
+    const double tr = true_residual(o, s, uB, uX, nullptr, st, adjoint);
+    inf.relres_true = tr / ortho_res0;
+  }
   if (inf.status == KR_MAXIT && inf.relres_true > 1.0) inf.status = KR_DIVERGED;
   if (!std::isfinite(inf.relres_true) && inf.status != KR_BREAKDOWN) inf.status = KR_NAN;
+  inf.breakdown_iter = inf.status == KR_BREAKDOWN ? inf.iters + 1 : 0;
   if (opt.host_buffers) {
     KR_CUDA(cudaMemcpyAsync(X, tX, bytes, cudaMemcpyDeviceToHost, st));
     KR_CUDA(cudaStreamSynchronize(st));

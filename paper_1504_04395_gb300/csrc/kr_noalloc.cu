@@ -14,9 +14,17 @@
 //    held by every GPU on which the library is loaded until the process exits;
 //  * s <= 16 (a Gram needs s*s <= 256 slots per CTA); larger s is rejected with
 //    KR_UNSUPPORTED, before any GPU work;
-//  * the first call on a device looks up the device address of the array once
-//    (cudaGetSymbolAddress, with that device current) and caches it; make that
-//    first call before any stream capture;
+//  * the call runs on the device that holds Y (made current for the call and the
+//    previous device restored); U, out and a non-null stream must belong to the same
+//    device, otherwise KR_BAD_ARG before any GPU work;
+//  * the device address of the array is looked up (cudaGetSymbolAddress, with that
+//    device current) on every call that is not being captured into a CUDA graph, so a
+//    device reset or a new primary context does not leave a stale address behind;
+//    while a stream capture is in progress the address of the last uncaptured call on
+//    that device is used, so make one call on each device before capturing;
+//  * the grid is capped at 256 CTAs (kr_block_reduce uses up to 4 CTAs per SM), so for
+//    large n the partial sums are grouped differently: results agree with
+//    kr_block_reduce to rounding, not bitwise;
 //  * all calls share the one array: every CTA overwrites all of its slots, so
 //    nothing needs clearing between calls, but calls whose GPU work overlaps
 //    (different streams, or different host threads) race on the array.
@@ -38,22 +46,54 @@ static __device__ __align__(256) double2 g_noalloc_partials[kNoAllocMaxCtas * kN
 std::mutex g_noalloc_mu;
 double2* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
-// Device address of g_noalloc_partials on the current device (looked up once per device).
-cudaError_t noalloc_scratch(double2** out) {
+// Device address of g_noalloc_partials on the current device.  Looked up again on every
+// call outside a stream capture (cheap; survives a device reset); during a capture the
+// address recorded by the last uncaptured call on this device is used.
+cudaError_t noalloc_scratch(bool capturing, double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_ptr[dev] == nullptr) {
+  if (!capturing) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = reinterpret_cast<double2*>(p);
+  } else if (g_noalloc_ptr[dev] == nullptr) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
 }
+
+// Device that holds a pointer (-1: not device-accessible memory the runtime knows of).
+int pointer_device(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the (non-sticky) error left by the failed query
+    return -1;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return -1;
+  return at.device;
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the previous device.
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  cudaError_t enter(int dev) {
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return e;
+    if (prev == dev) return cudaSuccess;
+    e = cudaSetDevice(dev);
+    switched = e == cudaSuccess;
+    return e;
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
 
 template <int G, int NG>
 void launch_noalloc(const LinArgs& a, const RedSet& rs, int grid, cudaStream_t st) {
@@ -82,13 +122,40 @@ extern "C" kr_status kr_block_reduce_noalloc(int64_t n, int32_t s, const double*
     set_error("kr_block_reduce_noalloc: s must be in [1, 16] (static scratch holds 256 slots per CTA)");
     return KR_UNSUPPORTED;
   }
-  double2* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // every operand on one device, the one the call runs on
+  const int dev = pointer_device(Y);
+  if (dev < 0 || pointer_device(out) != dev || (kind != KR_RED_NORM2 && pointer_device(U) != dev)) {
+    set_error("kr_block_reduce_noalloc: U, Y and out must be device memory of one GPU");
+    return KR_BAD_ARG;
+  }
+  if (st != nullptr) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess || sdev != dev) {
+      cudaGetLastError();
+      set_error("kr_block_reduce_noalloc: the stream does not belong to the device that holds Y");
+      return KR_BAD_ARG;
+    }
+  }
+  DeviceGuard guard;
+  cudaError_t e = guard.enter(dev);
   if (e != cudaSuccess) {
-    set_error(std::string("kr_block_reduce_noalloc: scratch lookup failed: ") + cudaGetErrorString(e));
+    set_error(std::string("kr_block_reduce_noalloc: cannot select the device of Y: ") + cudaGetErrorString(e));
     return KR_CUDA_ERROR;
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) {
+    set_error(std::string("kr_block_reduce_noalloc: stream query failed: ") + cudaGetErrorString(e));
+    return KR_CUDA_ERROR;
+  }
+  double2* scratch = nullptr;
+  e = noalloc_scratch(cap != cudaStreamCaptureStatusNone, &scratch);
+  if (e != cudaSuccess) {
+    set_error(std::string("kr_block_reduce_noalloc: scratch lookup failed (during a stream capture the first "
+                          "call on a device must have been made before the capture): ") + cudaGetErrorString(e));
+    return KR_CUDA_ERROR;
+  }
   LinArgs a{};
   a.n = n;
   a.s = s;

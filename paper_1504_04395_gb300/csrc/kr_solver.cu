@@ -252,7 +252,11 @@ constexpr int kMaxSlots = 2 * kMaxS * kMaxS + 4 * kMaxS + 8;
 constexpr int kRedCap = 1 << 16;
 
 Workspace& get_workspace(Operator& op, int s, size_t elem, int nblocks, int nvecs, int maxit) {
+  // elem is the key of the workspace: 8 (complex64) and 16 (complex128) are the solvers' own;
+  // larger values name further complex128 workspaces (defect correction, preconditioning,
+  // orthonormalised right-hand sides), whose blocks hold complex128 entries
   const long long key = (long long)s * 64 + (long long)elem;
+  if (elem > sizeof(double2)) elem = sizeof(double2);
   auto it = op.ws.find(key);
   if (it == op.ws.end()) {
     auto w = std::make_unique<Workspace>();
@@ -1573,6 +1577,41 @@ void standalone_qr(Operator& op, Workspace& ws, int64_t n, int s, void* Q, cudaS
   Engine<double> E(op, false, s, st, ws);
   E.n = n;
   E.thin_qr(Q, SL_QR_S);
+}
+
+// Orthonormalised right-hand sides (the set-up of Sec. 5: B replaced by the factor Q of a thin
+// QR).  R_0 = B - op(A) X_0 is formed in block 0 of a workspace of its own and factorised in
+// place, R_0 = Q S, with S kept in that workspace's arena; block 1 is zeroed for the solution Y
+// of op(A) Y = Q.  Returns ||R_0||_F, or a negative value when R_0 is numerically rank deficient.
+double orthonormal_rhs(Operator& op, int s, const void* B, const void* X, void** Q, void** Y, cudaStream_t st,
+                       bool adjoint) {
+  Workspace& ws = get_workspace(op, s, kOrthoKey, 2, 0, 1);
+  *Q = ws.blocks[0];
+  *Y = ws.blocks[1];
+  const double res0 = true_residual(op, s, B, X, *Q, st, adjoint);
+  KR_CUDA(cudaMemsetAsync(*Y, 0, sizeof(double2) * (size_t)op.n * s, st));
+  if (!(res0 > 0.0)) return res0;  // zero (X_0 solves the system) or non-finite: nothing to factorise
+  DevState h{};
+  h.maxit = 1;
+  KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  standalone_qr(op, ws, op.n, s, *Q, st);
+  DevState back{};
+  KR_CUDA(cudaMemcpyAsync(&back, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  KR_CUDA(cudaStreamSynchronize(st));
+  return (back.done && back.status == 1) ? -1.0 : res0;
+}
+
+// X += Y S with Y and S from the last orthonormal_rhs on this operator and s
+void add_back_rhs_factor(Operator& op, int s, void* X, cudaStream_t st) {
+  Workspace& ws = get_workspace(op, s, kOrthoKey, 2, 0, 1);
+  Engine<double> E(op, false, s, st, ws);
+  DevState h{};
+  KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  Lin L(op.n, s);
+  const int o = L.out(X);
+  L.blk(o, X);
+  L.blk(o, ws.blocks[1], mat(E.slot(SL_QR_S)));
+  E.lin(L);
 }
 
 // ||B - op(A) X||_F in FP64 (R written to Rbuf when given)

@@ -40,6 +40,13 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
                    bool adjoint);
 
 double true_residual(Operator& op, int s, const void* B, const void* X, void* Rbuf, cudaStream_t st, bool adjoint);
+
+// workspace key (element size field) of the orthonormalised right-hand sides: a workspace of its
+// own, so that the solve that follows cannot overwrite Q, Y or S
+constexpr size_t kOrthoKey = 32;
+double orthonormal_rhs(Operator& op, int s, const void* B, const void* X, void** Q, void** Y, cudaStream_t st,
+                       bool adjoint);
+void add_back_rhs_factor(Operator& op, int s, void* X, cudaStream_t st);
 void ensure_orig_pattern(Operator& op);
 void rebuild_operator_values(Operator& op);
 void standalone_qr(Operator& op, Workspace& ws, int64_t n, int s, void* Q, cudaStream_t st);
