@@ -3,9 +3,10 @@
 16^4 sites x 12 unknowns (n = 786,432, 49 non-zeros per row, mass chosen so the
 spectrum stays in the right half-plane), s = 12 point sources and s = 12 Gaussian right-hand
 sides, eGl-BiCG, eGl-QMR and Bl-BiCGStab-rQ to 1e-8: convergence with the true
-residual recomputed in FP64, and the first iterations against the oracle on the same
-full-size inputs.  Mixed precision (complex64 inner solves, FP64 defect correction)
-against the FP64 GPU path on the same lattice with s = 32.
+residual recomputed in FP64, and the iterations against the oracle on the same full-size
+inputs (20 for the economic methods).  Mixed precision (complex64 inner solves, FP64 defect
+correction) with s = 32: its residual recomputed with the oracle's matrix, and the FP64 GPU
+path.
 """
 import numpy as np
 import pytest
@@ -78,22 +79,40 @@ def test_point_sources_mean_shadow_is_degenerate(lat):
     assert ref.status != oracle.Status.OK and info.status != "OK"
 
 
-@pytest.mark.parametrize("method", ["egl_bicg", "egl_qmr", "bl_bicgstab_rq"])
-def test_config3_first_iterations_match_oracle(lat, method):
+# iterations compared with the oracle at the plain bar (1e-10 per iteration, 1e-8 on X).  Measured
+# with the oracle on this input: under a one-ulp change of B its own eGl-BiCG / eGl-QMR histories move
+# by at most 1e-11 relative over 20 iterations, Bl-BiCGStab-rQ's by 2e-10 at iteration 5, 3e-9 at 9
+# and 7e-7 at 19 (its s x s systems R~^H W lose conditioning fast on the lattice), so no FP64 program
+# can be held to 1e-10 there beyond the first 4 iterations.
+CONFIG3_WINDOW = {"egl_bicg": 20, "egl_qmr": 20, "bl_bicgstab_rq": 4}
+
+
+@pytest.mark.parametrize("method", list(CONFIG3_WINDOW))
+def test_config3_iterations_match_oracle(lat, method):
     kr, L, rp, ci, v, op = lat
     B = rhs("gauss", L)
     A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
-    ref = oracle.solve(method, A, B, tol=0.0, maxit=2)
-    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=0.0, maxit=2)
-    assert np.allclose(info.history, ref.history, rtol=1e-10, atol=0)
-    assert np.linalg.norm(X.cpu().numpy() - ref.X) / np.linalg.norm(ref.X) < 1e-10
+    k = CONFIG3_WINDOW[method]
+    ref = oracle.solve(method, A, B, tol=0.0, maxit=k)
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=0.0, maxit=k)
+    assert info.iters == ref.iters == k
+    a, b = np.array(info.history), np.array(ref.history)
+    assert np.all(np.abs(a - b) <= 1e-10 * b), float(np.max(np.abs(a - b) / b))
+    assert np.linalg.norm(X.cpu().numpy() - ref.X) / np.linalg.norm(ref.X) < 1e-8
 
 
 def test_mixed_precision_vs_fp64_on_lattice(lat):
+    """Mixed precision (complex64 inner solves to 1e-4, FP64 defect correction to 1e-10) on the 16^4
+    lattice with s = 32: the residual of the result recomputed on the host with the oracle's sparse
+    matrix in FP64, and the result against the pure-FP64 GPU solve."""
     kr, L, rp, ci, v, op = lat
-    B = torch.from_numpy(gaussian_block(L.n, 32, seed=32)).cuda()
+    Bh = gaussian_block(L.n, 32, seed=32)
+    B = torch.from_numpy(Bh).cuda()
     X64, i64 = kr.kr_solve(op, "egl_bicg", B, tol=1e-10, maxit=4000)
     X32, i32 = kr.kr_solve(op, "egl_bicg", B, tol=1e-10, maxit=4000, precision=kr.FP32_REFINE, inner_tol=1e-4)
     assert i64.status == "OK" and i32.status == "OK", (i64, i32)
     assert i32.relres_true <= 1e-10
+    A = oracle.csr_matrix_from_arrays(L.n, rp, ci, v)
+    Xn = X32.cpu().numpy()
+    assert np.linalg.norm(Bh - oracle.spmm(A, Xn)) / np.linalg.norm(Bh) <= 1.1e-10
     assert float(torch.linalg.norm(X32 - X64) / torch.linalg.norm(X64)) < 1e-8
