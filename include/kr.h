@@ -347,6 +347,35 @@ KR_API kr_status kr_profile_read(kr_profile* out, int32_t reset);
  * returns KR_OK. */
 KR_API kr_status kr_set_column_pairs(int32_t enable);
 
+/* Kernel choice for complex64 CSR products (the paper has no counterpart).  With enable != 0
+ * (the default), complex64 products of a CSR operator with s in {2, 4, 8, 16, 32}, at most
+ * 1024 stored entries per tile of rows (128, 64 or 32 rows for s <= 8, 16, 32), at most two
+ * fused s x s Grams and two distinct block operands of the fused reductions run on a kernel
+ * that stages each row tile's row pointers, diagonal, indices, values and reduction operands
+ * in shared memory with bulk asynchronous copies and forms the fused Grams from shared memory;
+ * enable == 0 leaves them to the column-pair and one-column kernels (kr_set_column_pairs).
+ * Products are bitwise the same on all of them; reductions agree to FP32 rounding.
+ * Process-wide; always returns KR_OK. */
+KR_API kr_status kr_set_tile_kernels(int32_t enable);
+
+/* Schedule of Gl-BiCG (Algorithm 2) and eGl-BiCG (Algorithm 4); the paper has no counterpart.
+ * With enable != 0 (the default) alpha's denominator tr(Ph^H A P) is taken as tr((A^H Ph)^H P),
+ * a reduction of the direction update of P once A^H Ph is formed, and the update X += alpha P,
+ * R -= alpha A P, Rh -= conj(alpha) A^H Ph runs in one pass that forms A P row by row without
+ * storing it (CSR and stencil operators without preconditioner; otherwise A P is stored first).
+ * Per iteration that reads and writes 2M + 8 Bv instead of 2M + 11 Bv for eGl-BiCG and
+ * 2M + 17 Bv instead of 2M + 19 Bv for Gl-BiCG (M: one read of A, Bv: one n x s block).  The
+ * iterates are those of the algorithms in exact arithmetic; rounding differs.  enable == 0
+ * runs the algorithms' own order.  Process-wide; always returns KR_OK. */
+KR_API kr_status kr_set_fused_products(int32_t enable);
+
+/* Number of bounded waits of the tile kernels (kr_set_tile_kernels) that ran out since the last
+ * reset, for the current device.  A wait that runs out means the copies it waited for did not
+ * arrive within about a second; the kernel then stops without computing the rest of its tiles and
+ * writes NaN into its partial reductions, so the affected results are not silently wrong.  With
+ * reset != 0 the counter is cleared.  KR_BAD_ARG if count is NULL. */
+KR_API kr_status kr_take_device_timeouts(int32_t reset, int64_t* count);
+
 /* Kernel choice for the matrix-free lattice product (kr_op_create_lattice4d); the paper
  * has no counterpart.  rows = 4: a thread forms the 4 rows of one (site, colour) pair of
  * one column (fewer registers, the spin projection repeated per colour); rows = 12: a
@@ -354,6 +383,14 @@ KR_API kr_status kr_set_column_pairs(int32_t enable);
  * registers); rows = 0 (the default): 12, measured faster in both precisions.
  * Process-wide; returns KR_BAD_ARG for other values. */
 KR_API kr_status kr_set_lattice_rows_per_thread(int32_t rows);
+
+/* Arithmetic-throughput probe (a diagnostic; the paper has no counterpart): one launch of
+ * 4 CTAs x 256 threads per SM, each thread running 16 independent FMA chains of `iters` steps
+ * in FP64 (precision = KR_FP64) or FP32 (precision = 2), enqueued on `stream`.  *flops receives
+ * the launch's floating-point operations (2 per FMA), so that the caller's CUDA-event time
+ * gives the device's FMA rate: the denominator of the FP64 path's roofline.  out: device
+ * buffer of one double (written by one thread).  KR_BAD_ARG for other arguments. */
+KR_API kr_status kr_probe_fma(int32_t precision, int64_t iters, double* out, double* flops, void* stream);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 KR_API const char* kr_last_error(void);

@@ -108,6 +108,10 @@ SIGNATURES = {
     "kr_op_apply_precond": (_I32, [_P, _I32, _I32, _P, _P, _P]),
     "kr_set_lattice_rows_per_thread": (_I32, [_I32]),
     "kr_profile_read": (_I32, [ctypes.POINTER(KrProfile), _I32]),
+    "kr_probe_fma": (_I32, [_I32, _I64, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "kr_set_tile_kernels": (_I32, [_I32]),
+    "kr_set_fused_products": (_I32, [_I32]),
+    "kr_take_device_timeouts": (_I32, [_I32, ctypes.POINTER(_I64)]),
 }
 
 
@@ -561,9 +565,37 @@ def kr_set_column_pairs(enable=True):
     _check(lib().kr_set_column_pairs(int(bool(enable))))
 
 
+def kr_set_tile_kernels(enable=True):
+    """Run complex64 CSR products on the TMA-staged row-tile kernel where it applies (default on)."""
+    _check(lib().kr_set_tile_kernels(int(bool(enable))))
+
+
+def kr_set_fused_products(enable=True):
+    """Gl-/eGl-BiCG with alpha from the adjoint product and the update fused with A P (default on)."""
+    _check(lib().kr_set_fused_products(int(bool(enable))))
+
+
+def kr_take_device_timeouts(reset=True):
+    """Bounded device waits of the tile kernels that ran out since the last reset (0 normally)."""
+    c = ctypes.c_int64()
+    _check(lib().kr_take_device_timeouts(int(bool(reset)), ctypes.byref(c)))
+    return c.value
+
+
 def kr_set_lattice_rows_per_thread(rows=0):
     """Matrix-free lattice kernel: 4 rows per thread, 12 (whole sites) or 0 (default per precision)."""
     _check(lib().kr_set_lattice_rows_per_thread(int(rows)))
+
+
+def kr_probe_fma(precision="fp64", iters=1 << 19, stream=None):
+    """Launch the FMA-throughput probe once; returns (flops of the launch, device buffer).  Time it
+    with CUDA events on `stream` to obtain the FP64 (or "fp32") FMA rate."""
+    torch = _torch()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fl = ctypes.c_double()
+    _check(lib().kr_probe_fma(0 if precision == "fp64" else 2, int(iters), ctypes.c_void_p(out.data_ptr()),
+                              ctypes.byref(fl), _stream(stream)))
+    return fl.value, out
 
 
 def kr_profile_read(reset=False):
@@ -582,4 +614,5 @@ __all__ = [
     "kr_op_create_csr", "kr_op_update_values", "kr_op_apply", "kr_op_apply_reduce", "kr_block_reduce", "kr_thin_qr",
     "kr_solve", "kr_adjoint_solve", "kr_grad_values", "kr_last_error", "solve", "adjoint_solve",
     "FP64", "FP32_REFINE", "kr_profile_enable", "kr_profile_read", "kr_set_column_pairs", "kr_op_apply_precond", "kr_set_lattice_rows_per_thread", "kr_op_apply_reduce_c64", "kr_block_reduce_c64", "KERNEL_CLASSES", "kr_block_reduce_noalloc",
+    "kr_probe_fma", "kr_set_tile_kernels", "kr_take_device_timeouts", "kr_set_fused_products",
 ]

@@ -182,6 +182,16 @@ kr_status kr_set_column_pairs(int32_t enable) {
   return KR_OK;
 }
 
+kr_status kr_set_tile_kernels(int32_t enable) {
+  kr::set_tile_kernels(enable != 0);
+  return KR_OK;
+}
+
+kr_status kr_set_fused_products(int32_t enable) {
+  kr::set_fused_products(enable != 0);
+  return KR_OK;
+}
+
 kr_status kr_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
                            const double* vals, int32_t device, kr_op* out) {
   if (!out) { set_error("out is NULL"); return KR_BAD_ARG; }

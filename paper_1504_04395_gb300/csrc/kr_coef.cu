@@ -176,6 +176,15 @@ __global__ void __launch_bounds__(256) coef_kernel(CoefArgs a) {
       }
       break;
     }
+    case PH_SC_ALPHA_CONJ: {  // alpha = rho / conj(red): the denominator's reduction came conjugated
+      if (threadIdx.x == 0) {
+        double2 al;
+        const double2 d = make_double2(red[a.i0].x, -red[a.i0].y);
+        const int r = check_div(st->sc_rho, d, &al);
+        if (r) { st->status = r; st->done = 1; } else SLP(a, SL_ALPHA)[0] = al;
+      }
+      break;
+    }
     case PH_SC_BETA: {
       monitor(a, sqrt(red[a.i1].x));
       if (is_done(st)) break;

@@ -71,6 +71,7 @@ enum Phase : int {
   PH_QMR_INIT, PH_QMR_DELTA, PH_QMR_COEF1, PH_QMR_COEF2, PH_QMR_MON,   // Gl/eGl-QMR
   PH_BQ_INIT, PH_BQ_COEF1, PH_BQ_COEF2, PH_BQ_MON,     // Bl-QMR
   PH_FILL_ONES,
+  PH_SC_ALPHA_CONJ,                                    // Gl-BiCG with alpha from the adjoint product
 };
 
 struct CoefArgs {
@@ -87,10 +88,15 @@ struct CoefArgs {
 void launch_coef(const CoefArgs& a, cudaStream_t st);
 
 // ----- operator ---------------------------------------------------------------------------
+constexpr size_t kCsrPad = 64;
+
 template <typename T>
 struct CsrDev {
   int64_t n = 0, nnz = 0;
+  int64_t maxrow = 0;     // most stored entries in one row
   int split = 0;
+  // the arrays are allocated kCsrPad bytes longer than their contents, so that 16-byte
+  // rounded bulk copies of a row range never read past an allocation
   int64_t* rowptr = nullptr;
   int32_t* colidx = nullptr;
   C2<T>* vals = nullptr;  // split == 0

@@ -49,6 +49,13 @@ inline int row_grid(int64_t n, int s) {
 // complex64 row kernels on column pairs (kr_set_column_pairs; on by default)
 bool pair_kernels_enabled();
 void set_pair_kernels(bool on);
+// Gl-/eGl-BiCG with alpha from the adjoint product and the update fused with the product
+// (kr_set_fused_products; on by default)
+bool fused_products_enabled();
+void set_fused_products(bool on);
+// complex64 CSR products on TMA-staged row tiles (kr_set_tile_kernels; on by default)
+bool tile_kernels_enabled();
+void set_tile_kernels(bool on);
 // rows per thread of the matrix-free lattice product (4: (site, colour) units, 12: whole sites)
 int lattice_rows_per_thread(size_t real_bytes);
 void set_lattice_rows_per_thread(int rows);
@@ -62,6 +69,10 @@ template <typename T>
 int launch_lincomb(const LinArgs& a, const RedSet& rs, int grid, const int* done, cudaStream_t st);
 template <typename T>
 void launch_reduce(const void* partials, int nparts, int nslots, double2* out, const int* done, cudaStream_t st);
+// row-local combination with SRC_SPMM terms: the product of sp formed in the same pass
+template <typename T>
+int launch_lincomb_spmm(const LinArgs& a, const RedSet& rs, const SpmmArgs<T>& sp, int grid, const int* done,
+                        cudaStream_t st);
 
 // number of GRAM reductions in a set
 inline int count_grams(const RedSet& rs) {

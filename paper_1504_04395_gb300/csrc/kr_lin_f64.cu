@@ -1,0 +1,5 @@
+// complex128 instantiation of the row-local linear combinations
+#include "kr_rows_launch.cuh"
+namespace kr {
+KR_INSTANTIATE_LIN(double)
+}

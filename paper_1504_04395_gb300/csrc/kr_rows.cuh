@@ -69,6 +69,7 @@ struct SpmmArgs {
   const double2* ys;         // optional device scalar multiplying ay (complex)
   int ys_conj, ys_neg;
   int64_t nnz;               // stored entries (host-side bookkeeping for the launch profile)
+  int64_t maxrow;            // most stored entries in one row (CSR; host-side kernel choice)
   // matrix-free (2d+1)-point stencil with Dirichlet boundaries (nst = d > 0 replaces the CSR):
   // y_j = c V_j + sum_a m_a V_{j - st_a} [x_a > 0] + p_a V_{j + st_a} [x_a < N_a - 1]
   int nst;
@@ -91,7 +92,9 @@ struct SpmmArgs {
 // ---------------------------------------------------------------------------------------
 // Linear combinations: out_o = sum_t  src_t * coef_t
 // ---------------------------------------------------------------------------------------
-enum SrcKind : int { SRC_BLOCK = 0, SRC_VEC = 1, SRC_REG = 2 };
+// SRC_SPMM: the value (A V)[j][c] of the launch's sparse product, computed in the same pass
+// (the product operand is a separate kernel argument); it needs no memory block of its own.
+enum SrcKind : int { SRC_BLOCK = 0, SRC_VEC = 1, SRC_REG = 2, SRC_SPMM = 3 };
 enum CoefKind : int { COEF_ONE = 0, COEF_SCALAR = 1, COEF_MAT = 2, COEF_DIAG = 3, COEF_REAL = 4 };
 
 struct Term {

@@ -144,6 +144,111 @@ __device__ __forceinline__ C2<T> scalar_coef(const double2* p, int conj, int neg
 // ---------------------------------------------------------------------------------------
 // SpMM with fused reductions
 // ---------------------------------------------------------------------------------------
+
+// Stencil coefficients in the element type, converted once per CTA (a double -> float
+// conversion runs on the FP64 pipe): centre, minus neighbours, plus neighbours per axis.
+template <typename T>
+struct StencilCoef {
+  C2<T> c, m[3], p[3];
+};
+template <typename T>
+__device__ __forceinline__ StencilCoef<T> stencil_coef(const SpmmArgs<T>& a) {
+  StencilCoef<T> k;
+  k.c = mk<T>((T)a.sc.x, (T)a.sc.y);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    k.m[q] = mk<T>((T)a.sm[q].x, (T)a.sm[q].y);
+    k.p[q] = mk<T>((T)a.sp[q].x, (T)a.sp[q].y);
+  }
+  return k;
+}
+
+// (A V)[j][c] for one thread of row j's group (G threads per row): the matrix-free stencil or
+// the CSR product, before any scaling.  act = row j exists and c < s; rowok = row j exists.
+template <typename T, int G>
+__device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoef<T>& sk, int64_t j, int c,
+                                          bool rowok, bool act) {
+  const int s = a.s;
+  C2<T> y = czero<T>();
+  if (rowok && a.nst > 0) {
+    // matrix-free stencil, same summation order as the real-off-diagonal CSR storage:
+    // centre, then -axis d-1 .. -axis 0, then +axis 0 .. +axis d-1
+    const C2<T> stc = sk.c;
+    int64_t xc[3];
+    int64_t rem = j;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
+    }
+    if (act) {
+      y = cmul<T>(stc, a.V[j * s + c]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int qa = 2 - q;
+        if (qa < a.nst && xc[qa] > 0) {
+          const C2<T> xv = a.V[(j - a.sstr[qa]) * s + c];
+          const C2<T> m = sk.m[qa];
+          if (a.sreal) y = cfmareal<T>(m.x, xv, y);
+          else y = cfma<T>(m, xv, y);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < a.nst && xc[q] < a.sdims[q] - 1) {
+          const C2<T> xv = a.V[(j + a.sstr[q]) * s + c];
+          const C2<T> pp = sk.p[q];
+          if (a.sreal) y = cfmareal<T>(pp.x, xv, y);
+          else y = cfma<T>(pp, xv, y);
+        }
+      }
+    }
+  } else if (rowok) {
+    const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
+    // batches of kBatch entries: all index, value and gathered-row loads of a batch are
+    // issued before its FMAs, so several neighbour rows are in flight per thread
+    constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
+    if (a.split) {
+      if (act) y = cmul<T>(a.diag[j], a.V[j * s + c]);
+      for (int64_t k = k0; k < k1; k += kBatch) {
+        int32_t col[kBatch];
+        T v[kBatch];
+        C2<T> x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const bool in = k + u < k1;
+          col[u] = in ? a.colidx[k + u] : 0;
+          v[u] = in ? a.offr[k + u] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+          x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+          if (act && k + u < k1) y = cfmareal<T>(v[u], x[u], y);
+      }
+    } else {
+      for (int64_t k = k0; k < k1; k += kBatch) {
+        int32_t col[kBatch];
+        C2<T> v[kBatch];
+        C2<T> x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const bool in = k + u < k1;
+          col[u] = in ? a.colidx[k + u] : 0;
+          v[u] = in ? a.vals[k + u] : czero<T>();
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+          x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+          if (act && k + u < k1) y = cfma<T>(v[u], x[u], y);
+      }
+    }
+  }
+  return y;
+}
+
 template <typename T, int G, int NG>
 __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs, const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
@@ -162,109 +267,22 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
     ysc = mk<T>((T)a.ay * d.x, (T)a.ay * d.y);
   }
   const T bz = (T)a.bz;
-  // stencil coefficients converted once (a double -> float conversion runs on the FP64 pipe)
-  C2<T> stc = mk<T>((T)a.sc.x, (T)a.sc.y), stm[3], stp[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    stm[q] = mk<T>((T)a.sm[q].x, (T)a.sm[q].y);
-    stp[q] = mk<T>((T)a.sp[q].x, (T)a.sp[q].y);
-  }
+  const StencilCoef<T> sk = stencil_coef<T>(a);
   Acc<T, G, NG> acc;
   acc_zero(acc);
   for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
-    C2<T> y = czero<T>();
-    if (rowok && a.nst > 0) {
-      // matrix-free stencil, same summation order as the real-off-diagonal CSR storage:
-      // centre, then -axis d-1 .. -axis 0, then +axis 0 .. +axis d-1
-      int64_t xc[3];
-      int64_t rem = j;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
+    C2<T> y = spmm_row<T, G>(a, sk, j, c, rowok, act);
+    if (act) {
+      if (scaled) y = cmul<T>(ysc, y);
+      if (a.Z != nullptr) {
+        const C2<T> z = a.Z[j * s + c];
+        y.x = fma(bz, z.x, y.x);
+        y.y = fma(bz, z.y, y.y);
       }
-      if (act) {
-        // neighbours one at a time: FMA order centre, -axis d-1..0, +axis 0..d-1
-        y = cmul<T>(stc, a.V[j * s + c]);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int qa = 2 - q;
-          if (qa < a.nst && xc[qa] > 0) {
-            const C2<T> xv = a.V[(j - a.sstr[qa]) * s + c];
-            if (a.sreal) y = cfmareal<T>(stm[qa].x, xv, y);
-            else y = cfma<T>(stm[qa], xv, y);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q < a.nst && xc[q] < a.sdims[q] - 1) {
-            const C2<T> xv = a.V[(j + a.sstr[q]) * s + c];
-            if (a.sreal) y = cfmareal<T>(stp[q].x, xv, y);
-            else y = cfma<T>(stp[q], xv, y);
-          }
-        }
-        if (scaled) y = cmul<T>(ysc, y);
-        if (a.Z != nullptr) {
-          const C2<T> z = a.Z[j * s + c];
-          y.x = fma(bz, z.x, y.x);
-          y.y = fma(bz, z.y, y.y);
-        }
-        if (a.Y != nullptr) a.Y[j * s + c] = y;
-      }
-    } else if (rowok) {
-      const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
-      // batches of kBatch entries: all index, value and gathered-row loads of a batch are
-      // issued before its FMAs, so several neighbour rows are in flight per thread
-      constexpr int kBatch = sizeof(T) == 4 ? 4 : 2;
-      if (a.split) {
-        if (act) y = cmul<T>(a.diag[j], a.V[j * s + c]);
-        for (int64_t k = k0; k < k1; k += kBatch) {
-          int32_t col[kBatch];
-          T v[kBatch];
-          C2<T> x[kBatch];
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u) {
-            const bool in = k + u < k1;
-            col[u] = in ? a.colidx[k + u] : 0;
-            v[u] = in ? a.offr[k + u] : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u)
-            x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u)
-            if (act && k + u < k1) y = cfmareal<T>(v[u], x[u], y);
-        }
-      } else {
-        for (int64_t k = k0; k < k1; k += kBatch) {
-          int32_t col[kBatch];
-          C2<T> v[kBatch];
-          C2<T> x[kBatch];
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u) {
-            const bool in = k + u < k1;
-            col[u] = in ? a.colidx[k + u] : 0;
-            v[u] = in ? a.vals[k + u] : czero<T>();
-          }
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u)
-            x[u] = (act && k + u < k1) ? a.V[(int64_t)col[u] * s + c] : czero<T>();
-#pragma unroll
-          for (int u = 0; u < kBatch; ++u)
-            if (act && k + u < k1) y = cfma<T>(v[u], x[u], y);
-        }
-      }
-      if (act) {
-        if (scaled) y = cmul<T>(ysc, y);
-        if (a.Z != nullptr) {
-          const C2<T> z = a.Z[j * s + c];
-          y.x = fma(bz, z.x, y.x);
-          y.y = fma(bz, z.y, y.y);
-        }
-        if (a.Y != nullptr) a.Y[j * s + c] = y;
-      }
+      if (a.Y != nullptr) a.Y[j * s + c] = y;
     }
     if (rs.nred > 0) {
 #pragma unroll
@@ -289,9 +307,9 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
 // ---------------------------------------------------------------------------------------
 // Row-local linear combinations with fused reductions
 // ---------------------------------------------------------------------------------------
-template <typename T, int G, int NG>
-__global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs, const int* done) {
-  if (done != nullptr && *(volatile const int*)done) return;
+// SP: the combination has SRC_SPMM terms, products of `sp` computed row by row in this pass
+template <typename T, int G, int NG, bool SP>
+__device__ __forceinline__ void lincomb_rows(const LinArgs& a, const RedSet& rs, const SpmmArgs<T>& sp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RPW = 32 / G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -322,12 +340,17 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
   __syncthreads();
   C2<T>* red_sm = Ms + a.nmat * ss;
   const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
+  StencilCoef<T> sk{};
+  if constexpr (SP) sk = stencil_coef<T>(sp);
   Acc<T, G, NG> acc;
   acc_zero(acc);
   for (int64_t base = (int64_t)blockIdx.x * rows_per_cta; base < n; base += (int64_t)gridDim.x * rows_per_cta) {
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
+    // the product's row, formed once (SRC_SPMM terms read it)
+    C2<T> yprod = czero<T>();
+    if constexpr (SP) yprod = spmm_row<T, G>(sp, sk, j, c, rowok, act);
     C2<T> o[kMaxOut];
 #pragma unroll
     for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();
@@ -345,6 +368,8 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
               x = pick<T>(o, t.src_reg);
             } else if (t.src_kind == SRC_BLOCK) {
               if (act) x = reinterpret_cast<const C2<T>*>(t.src)[j * s + c];
+            } else if (SP && t.src_kind == SRC_SPMM) {
+              x = yprod;
             } else {
               if (rowok) x = reinterpret_cast<const C2<T>*>(t.src)[j];
             }
@@ -406,6 +431,22 @@ __global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs,
     }
   }
   if (rs.nred > 0) cta_reduce<T, G, NG>(rs, acc, s, red_sm);
+}
+
+template <typename T, int G, int NG>
+__global__ void __launch_bounds__(kThreads) lincomb_kernel(LinArgs a, RedSet rs, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  SpmmArgs<T> none{};
+  lincomb_rows<T, G, NG, false>(a, rs, none);
+}
+
+// row-local combination whose terms include the sparse product (A V)[j] of `sp` (SRC_SPMM): the
+// product's rows are formed in the same pass and never stored
+template <typename T, int G, int NG>
+__global__ void __launch_bounds__(kThreads) lincomb_spmm_kernel(LinArgs a, RedSet rs, SpmmArgs<T> sp,
+                                                                const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  lincomb_rows<T, G, NG, true>(a, rs, sp);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -9,6 +9,7 @@
 #include "kr_rows_impl.cuh"
 #include "kr_rows_vec2.cuh"
 #include "kr_lattice.cuh"
+#include "kr_tile_c64.h"
 
 namespace kr {
 
@@ -200,6 +201,80 @@ static void lin2_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const i
   throw CudaError{cudaErrorInvalidValue, "lincomb: s out of range"};
 }
 
+// ---------------------------------------------------------------------------------------
+// complex64 CSR product on TMA-staged row tiles (kr_tile_c64.cuh)
+// ---------------------------------------------------------------------------------------
+inline int round16i(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
+
+// Shared-memory layout and reduction maps of a tile launch; false when the launch does not fit
+// the tile kernel (then the other kernels run it).
+static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L) {
+  if (a.nst > 0 || a.lat) return false;
+  const int s = a.s;
+  if (s != 4 && s != 8 && s != 16 && s != 32) return false;
+  const int GP = s / 2;
+  const int R = std::min(128, kTileThreadsMax / GP);
+  if ((int64_t)R * a.maxrow > kTileEcap) return false;
+  if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
+  if (rs.nred > kMaxRed) return false;
+  L = TileLayout{};
+  L.R = R;
+  int ngram = 0, nc = 0, nrow = 0;
+  for (int ri = 0; ri < kMaxRed; ++ri) L.red_u[ri] = -1;
+  for (int ri = 0; ri < rs.nred; ++ri) {
+    const RedSpec& r = rs.r[ri];
+    if (r.ureg >= 0) return false;
+    const bool block_u = r.kind == RED_GRAM || r.kind == RED_TRACE || r.kind == RED_CDOT;
+    int ui = -1;
+    if (block_u && r.U != nullptr && r.U != static_cast<const void*>(a.Y)) {
+      if (!aligned16(r.U)) return false;
+      for (int u = 0; u < L.nu; ++u)
+        if (L.U[u] == r.U) ui = u;
+      if (ui < 0) {
+        if (L.nu == kTileMaxU) return false;
+        ui = L.nu;
+        L.U[L.nu++] = r.U;
+      }
+    }
+    if (r.kind == RED_GRAM) {
+      if (ngram == 2) return false;
+      L.gram_u[ngram] = ui;
+      L.gram_slot[ngram] = r.slot;
+      ++ngram;
+    } else {
+      if (nrow == kTileRowReds) return false;
+      L.red_u[ri] = ui;
+      L.red_c[ri] = nc;
+      L.red_k[ri] = nrow++;
+      nc += (r.kind == RED_CDOT || r.kind == RED_GRAMV) ? s : 1;
+    }
+  }
+  L.ngram = ngram;
+  L.ystage = ngram > 0 ? 1 : 0;
+  L.ncompact = nc;
+  const bool split = a.split != 0;
+  L.off_rp = 0;
+  L.sz_rp = round16i((int64_t)(R + 2) * 8);
+  L.off_dg = L.sz_rp;
+  L.sz_dg = split ? R * 8 : 0;
+  L.off_u = L.sz_rp + L.sz_dg;
+  L.sz_u = R * s * 8;
+  L.off_col = 0;
+  L.sz_col = round16i((int64_t)(kTileEcap + 8) * 4);
+  L.off_val = L.sz_col;
+  L.sz_val = round16i((int64_t)(kTileEcap + 8) * (split ? 4 : 8));
+  const int strideA = L.sz_rp + L.sz_dg + L.nu * L.sz_u, strideB = L.sz_col + L.sz_val;
+  L.off_y = kTileStagesA * strideA + kTileStagesB * strideB;
+  const int staged = L.off_y + (L.ystage ? R * s * 8 : 0);
+  const int T = GP * R;
+  // Gram records: per (warp, row group of the warp) for s <= 16, per row group of the CTA for s = 32
+  const int nb = GP * GP;
+  const int nrec = GP <= 8 ? (T / 32) * (nb < 32 ? 32 / nb : 1) : T / nb;
+  const int final_red = (T / 32) * nc * 8 + ngram * nrec * s * s * 8;
+  L.total = std::max(staged, final_red);
+  return L.total <= kMaxDynSmem;
+}
+
 template <typename T>
 int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM, st);
@@ -209,6 +284,11 @@ int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* don
     done_launch = true;
   }
   if constexpr (sizeof(T) == 4) {
+    TileLayout L;
+    if (!done_launch && tile_kernels_enabled() && tile_layout(a, rs, L)) {
+      grid = launch_spmm_tile(a, rs, L, grid, done, st);
+      done_launch = true;
+    }
     if (!done_launch && pair_kernels_enabled() && pair_ok_spmm(a, rs)) {
       spmm2_dispatch(a, rs, grid, done, st);
       done_launch = true;
@@ -268,17 +348,11 @@ static void lin_ng(int ng, const LinArgs& a, const RedSet& rs, int& grid, const 
 template <typename T>
 static void lin_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st);
 
-template <typename T>
-int launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int* done, cudaStream_t st) {
-  LinArgs a = a_in;
-  RedSet rs = rs_in;
-  if (!resolve_sources(a, rs)) throw CudaError{cudaErrorInvalidValue, "lincomb: too many distinct operands"};
-  ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_LINCOMB32 : KC_LINCOMB, st);
-  if (sizeof(T) == 4 && pair_kernels_enabled() && pair_ok_lin(a, rs)) lin2_dispatch(a, rs, grid, done, st);
-  else lin_dispatch<T>(a, rs, grid, done, st);
-  const double E = sizeof(C2<T>);
+// profile accounting of a row-local launch (flops, bytes), shared by both launchers
+static void lin_account(const LinArgs& a, const RedSet& rs, double E, double& f, double& b) {
   const double n = (double)a.n, s = (double)a.s;
-  double f = 0.0, b = 0.0;
+  f = 0.0;
+  b = 0.0;
   const void* counted[kMaxOut * kMaxTerm + kMaxOut];
   int nc = 0;
   for (int o = 0; o < a.nout; ++o) {
@@ -292,7 +366,7 @@ int launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int
         case COEF_MAT: f += 8.0 * s * cnt; break;
         default: f += 8.0 * cnt; break;
       }
-      if (tm.src_kind != SRC_REG) {
+      if (tm.src_kind == SRC_BLOCK || tm.src_kind == SRC_VEC) {
         bool seen = false;
         for (int k = 0; k < nc; ++k) seen = seen || counted[k] == tm.src;
         if (!seen) {
@@ -305,6 +379,18 @@ int launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int
   }
   f += red_flops(rs, a.n, a.s);
   b += red_bytes(rs, a.n, a.s, E, counted, nc);
+}
+
+template <typename T>
+int launch_lincomb(const LinArgs& a_in, const RedSet& rs_in, int grid, const int* done, cudaStream_t st) {
+  LinArgs a = a_in;
+  RedSet rs = rs_in;
+  if (!resolve_sources(a, rs)) throw CudaError{cudaErrorInvalidValue, "lincomb: too many distinct operands"};
+  ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_LINCOMB32 : KC_LINCOMB, st);
+  if (sizeof(T) == 4 && pair_kernels_enabled() && pair_ok_lin(a, rs)) lin2_dispatch(a, rs, grid, done, st);
+  else lin_dispatch<T>(a, rs, grid, done, st);
+  double f = 0.0, b = 0.0;
+  lin_account(a, rs, sizeof(C2<T>), f, b);
   prof_end(tk, st, f, b);
   return grid;
 }
@@ -334,9 +420,11 @@ void launch_reduce(const void* partials, int nparts, int nslots, double2* out, c
   prof_end(tk, st, 2.0 * nparts * nslots, (double)sizeof(C2<T>) * nparts * nslots + 16.0 * nslots);
 }
 
+// products and reductions in one unit, row-local combinations in another (parallel build)
 #define KR_INSTANTIATE_ROWS(T)                                                                               \
   template int launch_spmm<T>(const SpmmArgs<T>&, const RedSet&, int, const int*, cudaStream_t);            \
-  template int launch_lincomb<T>(const LinArgs&, const RedSet&, int, const int*, cudaStream_t);             \
   template void launch_reduce<T>(const void*, int, int, double2*, const int*, cudaStream_t);
+#define KR_INSTANTIATE_LIN(T) \
+  template int launch_lincomb<T>(const LinArgs&, const RedSet&, int, const int*, cudaStream_t);
 
 }  // namespace kr

@@ -157,6 +157,136 @@ __device__ __forceinline__ void cta_reduce2(const RedSet& rs, Acc2<NR>& acc, int
   }
 }
 
+// (A V)[j] for the column pair p of row j (e = j * s + 2p, the pair's first element), before any
+// scaling: the matrix-free stencil (STENCIL) or the CSR product.  TAILBATCH: the last 1-3 entries
+// of a row as one predicated batch (needs registers; without it one entry at a time).
+template <bool STENCIL, bool TAILBATCH>
+__device__ __forceinline__ Pair spmm2_row(const SpmmArgs<float>& a, const float2 stc, const float2 (&stm)[3],
+                                          const float2 (&stp)[3], int64_t j, int p, int64_t e) {
+  const int s = a.s;
+  const int npairs = s / 2;
+  Pair y = pzero();
+  if constexpr (STENCIL) {
+    int64_t xc[3];
+    int64_t rem = j;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
+    const Pair xv = ld_pair(a.V, e);
+    y.a = cmul<float>(stc, xv.a);
+    y.b = cmul<float>(stc, xv.b);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int qa = 2 - q;
+      if (qa < a.nst && xc[qa] > 0) {
+        const Pair x = ld_pair(a.V, e - a.sstr[qa] * s);
+        if (a.sreal) { y.a = cfmareal<float>(stm[qa].x, x.a, y.a); y.b = cfmareal<float>(stm[qa].x, x.b, y.b); }
+        else { y.a = cfma<float>(stm[qa], x.a, y.a); y.b = cfma<float>(stm[qa], x.b, y.b); }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (q < a.nst && xc[q] < a.sdims[q] - 1) {
+        const Pair x = ld_pair(a.V, e + a.sstr[q] * s);
+        if (a.sreal) { y.a = cfmareal<float>(stp[q].x, x.a, y.a); y.b = cfmareal<float>(stp[q].x, x.b, y.b); }
+        else { y.a = cfma<float>(stp[q], x.a, y.a); y.b = cfma<float>(stp[q], x.b, y.b); }
+      }
+    }
+  } else {
+    const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
+    // gathers address V as float4 (one column pair) with 32-bit column indices:
+    // row c, pair p is element c * npairs + p (a 32 x 32 -> 64-bit multiply)
+    const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
+    const uint32_t np = (uint32_t)npairs;
+    auto gather = [&](int32_t c) {
+      const float4 v = Vq[(uint64_t)(uint32_t)c * np];
+      Pair q;
+      q.a = make_float2(v.x, v.y);
+      q.b = make_float2(v.z, v.w);
+      return q;
+    };
+    int64_t k = k0;
+    if (a.split) {
+      const float2 dgv = a.diag[j];
+      const Pair xv = ld_pair(a.V, e);
+      y.a = cmul<float>(dgv, xv.a);
+      y.b = cmul<float>(dgv, xv.b);
+      // full batches of four entries: indices, values and gathered pairs all in flight
+      for (; k + 4 <= k1; k += 4) {
+        int32_t col[4];
+        float v[4];
+        Pair x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
+      }
+      // the last 1-3 entries as one predicated batch: their loads are in flight together
+      // instead of one dependent index load and gather after another (with four
+      // accumulator slots this no longer fits the 64 registers: one entry at a time)
+      const int rem = (int)(k1 - k);
+      if constexpr (!TAILBATCH) {
+        for (; k < k1; ++k) {
+          const float v = a.offr[k];
+          const Pair x = gather(a.colidx[k]);
+          y.a = cfmareal<float>(v, x.a, y.a);
+          y.b = cfmareal<float>(v, x.b, y.b);
+        }
+      } else if (rem > 0) {
+        int32_t col[3];
+        float v[3];
+        Pair x[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) x[u] = gather(col[u]);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
+      }
+    } else {
+      for (; k + 4 <= k1; k += 4) {
+        int32_t col[4];
+        float2 v[4];
+        Pair x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
+      }
+      const int rem = (int)(k1 - k);
+      if constexpr (!TAILBATCH) {
+        for (; k < k1; ++k) {
+          const float2 v = a.vals[k];
+          const Pair x = gather(a.colidx[k]);
+          y.a = cfma<float>(v, x.a, y.a);
+          y.b = cfma<float>(v, x.b, y.b);
+        }
+      } else if (rem > 0) {
+        int32_t col[3];
+        float2 v[3];
+        Pair x[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) x[u] = gather(col[u]);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (u < rem) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
+      }
+    }
+  }
+  return y;
+}
+
 // ---------------------------------------------------------------------------------------
 // SpMM (CSR, real-off-diagonal CSR or stencil) on column pairs
 // ---------------------------------------------------------------------------------------
@@ -227,124 +357,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
       }
     }
     if (act) {
-      if constexpr (STENCIL) {
-        int64_t xc[3];
-        int64_t rem = j;
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
-        const Pair xv = ld_pair(a.V, e);
-        y.a = cmul<float>(stc, xv.a);
-        y.b = cmul<float>(stc, xv.b);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int qa = 2 - q;
-          if (qa < a.nst && xc[qa] > 0) {
-            const Pair x = ld_pair(a.V, e - a.sstr[qa] * s);
-            if (a.sreal) { y.a = cfmareal<float>(stm[qa].x, x.a, y.a); y.b = cfmareal<float>(stm[qa].x, x.b, y.b); }
-            else { y.a = cfma<float>(stm[qa], x.a, y.a); y.b = cfma<float>(stm[qa], x.b, y.b); }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q < a.nst && xc[q] < a.sdims[q] - 1) {
-            const Pair x = ld_pair(a.V, e + a.sstr[q] * s);
-            if (a.sreal) { y.a = cfmareal<float>(stp[q].x, x.a, y.a); y.b = cfmareal<float>(stp[q].x, x.b, y.b); }
-            else { y.a = cfma<float>(stp[q], x.a, y.a); y.b = cfma<float>(stp[q], x.b, y.b); }
-          }
-        }
-      } else {
-        const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
-        // gathers address V as float4 (one column pair) with 32-bit column indices:
-        // row c, pair p is element c * npairs + p (a 32 x 32 -> 64-bit multiply)
-        const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
-        const uint32_t np = (uint32_t)npairs;
-        auto gather = [&](int32_t c) {
-          const float4 v = Vq[(uint64_t)(uint32_t)c * np];
-          Pair q;
-          q.a = make_float2(v.x, v.y);
-          q.b = make_float2(v.z, v.w);
-          return q;
-        };
-        int64_t k = k0;
-        if (a.split) {
-          const float2 dgv = a.diag[j];
-          const Pair xv = ld_pair(a.V, e);
-          y.a = cmul<float>(dgv, xv.a);
-          y.b = cmul<float>(dgv, xv.b);
-          // full batches of four entries: indices, values and gathered pairs all in flight
-          for (; k + 4 <= k1; k += 4) {
-            int32_t col[4];
-            float v[4];
-            Pair x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
-          }
-          // the last 1-3 entries as one predicated batch: their loads are in flight together
-          // instead of one dependent index load and gather after another (with four
-          // accumulator slots this no longer fits the 64 registers: one entry at a time)
-          const int rem = (int)(k1 - k);
-          if constexpr (NR > 2) {
-            for (; k < k1; ++k) {
-              const float v = a.offr[k];
-              const Pair x = gather(a.colidx[k]);
-              y.a = cfmareal<float>(v, x.a, y.a);
-              y.b = cfmareal<float>(v, x.b, y.b);
-            }
-          } else if (rem > 0) {
-            int32_t col[3];
-            float v[3];
-            Pair x[3];
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.offr[k + u]; }
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) x[u] = gather(col[u]);
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) { y.a = cfmareal<float>(v[u], x[u].a, y.a); y.b = cfmareal<float>(v[u], x[u].b, y.b); }
-          }
-        } else {
-          for (; k + 4 <= k1; k += 4) {
-            int32_t col[4];
-            float2 v[4];
-            Pair x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = gather(col[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
-          }
-          const int rem = (int)(k1 - k);
-          if constexpr (NR > 2) {
-            for (; k < k1; ++k) {
-              const float2 v = a.vals[k];
-              const Pair x = gather(a.colidx[k]);
-              y.a = cfma<float>(v, x.a, y.a);
-              y.b = cfma<float>(v, x.b, y.b);
-            }
-          } else if (rem > 0) {
-            int32_t col[3];
-            float2 v[3];
-            Pair x[3];
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) { col[u] = a.colidx[k + u]; v[u] = a.vals[k + u]; }
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) x[u] = gather(col[u]);
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-              if (u < rem) { y.a = cfma<float>(v[u], x[u].a, y.a); y.b = cfma<float>(v[u], x[u].b, y.b); }
-          }
-        }
-      }
+      y = spmm2_row<STENCIL, (NR <= 2)>(a, stc, stm, stp, j, p, e);
       if (scaled) { y.a = cmul<float>(ysc, y.a); y.b = cmul<float>(ysc, y.b); }
       if (a.Z != nullptr) {
         const Pair z = ld_pair(a.Z, e);
@@ -379,9 +392,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) spmm2_kernel(SpmmArg
 // ---------------------------------------------------------------------------------------
 // Row-local linear combinations on column pairs (no s x s coefficient matrices)
 // ---------------------------------------------------------------------------------------
-template <int GP>
-__global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinArgs a, RedSet rs, const int* done) {
-  if (done != nullptr && *(volatile const int*)done) return;
+// SP: the combination has SRC_SPMM terms, products of `sp` formed row by row in this pass
+template <int GP, bool SP>
+__device__ __forceinline__ void lincomb2_rows(const LinArgs& a, const RedSet& rs, const SpmmArgs<float>& sp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int RPW = 32 / GP;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -409,6 +422,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
   __syncthreads();
   float2* red_sm = Dg + a.nmat * s;
   const int64_t rows_per_cta = (int64_t)(blockDim.x >> 5) * RPW;
+  // the product's stencil coefficients, converted once (double -> float runs on the FP64 pipe)
+  float2 stc = make_float2(0.f, 0.f), stm[3], stp[3];
+  if constexpr (SP) {
+    stc = make_float2((float)sp.sc.x, (float)sp.sc.y);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      stm[q] = make_float2((float)sp.sm[q].x, (float)sp.sm[q].y);
+      stp[q] = make_float2((float)sp.sp[q].x, (float)sp.sp[q].y);
+    }
+  }
   Acc2<> acc;
 #pragma unroll
   for (int q = 0; q < kMaxRed; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
@@ -442,6 +465,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
     const bool rowok = j < n;
     const bool act = rowok && p < npairs;
     const int64_t e = j * s + 2 * p;
+    // the product's row pair, formed once (SRC_SPMM terms read it)
+    Pair yprod = pzero();
+    if constexpr (SP) {
+      // the row's last 1-3 entries one at a time (fewer registers next to the outputs)
+      if (act) yprod = sp.nst > 0 ? spmm2_row<true, false>(sp, stc, stm, stp, j, p, e)
+                                  : spmm2_row<false, false>(sp, stc, stm, stp, j, p, e);
+    }
     // outputs as two register arrays (columns 2p and 2p + 1), selected with constant indices
     float2 oa[kMaxOut], ob[kMaxOut];
 #pragma unroll
@@ -461,6 +491,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
               x.b = pick<float>(ob, t.src_reg);
             } else if (t.src_kind == SRC_BLOCK) {
               if (act) x = ld_pair(reinterpret_cast<const float2*>(t.src), e);
+            } else if (SP && t.src_kind == SRC_SPMM) {
+              x = yprod;
             } else {
               if (act) { x.a = reinterpret_cast<const float2*>(t.src)[j]; x.b = x.a; }
             }
@@ -530,6 +562,23 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinA
   if (rs.nred > 0) cta_reduce2<GP, kMaxRed>(rs, acc, s, red_sm);
 }
 
+template <int GP>
+__global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_kernel(LinArgs a, RedSet rs, const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  SpmmArgs<float> none{};
+  lincomb2_rows<GP, false>(a, rs, none);
+}
+
+// column-pair combination whose terms include the sparse product of `sp` (SRC_SPMM), formed in
+// the same pass and never stored
+template <int GP>
+__global__ void __launch_bounds__(kThreads, kCtasPerSmRows) lincomb2_spmm_kernel(LinArgs a, RedSet rs,
+                                                                                 SpmmArgs<float> sp,
+                                                                                 const int* done) {
+  if (done != nullptr && *(volatile const int*)done) return;
+  lincomb2_rows<GP, true>(a, rs, sp);
+}
+
 // Can this launch run on column pairs?  Even s, 16-byte aligned blocks, no s x s Gram,
 // no s x s coefficient matrix and no n-vector output (those keep the one-column kernels).
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -557,6 +606,7 @@ inline bool pair_ok_lin(const LinArgs& a, const RedSet& rs) {
       const Term& tm = a.o[o].t[t];
       if (tm.coef_kind == COEF_MAT) return false;
       if (tm.src_kind == SRC_BLOCK && !aligned16(tm.src)) return false;
+      if (tm.src_kind == SRC_SPMM && tm.coef_kind == COEF_MAT) return false;
     }
   }
   return pair_ok_reds(rs);

@@ -103,6 +103,7 @@ SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s) {
   a.offr = M.offr;
   a.diag = M.diag;
   a.nnz = M.nnz;
+  a.maxrow = M.maxrow;
   return a;
 }
 template SpmmArgs<double> op_spmm_args<double>(const Operator&, bool, int);
@@ -154,9 +155,10 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
   if (!split) {
     std::vector<C2<T>> hv(d.nnz);
     for (int64_t k = 0; k < d.nnz; ++k) hv[k] = mk<T>((T)v[2 * k], (T)v[2 * k + 1]);
-    KR_CUDA(cudaMalloc(&d.rowptr, sizeof(int64_t) * (n + 1)));
-    KR_CUDA(cudaMalloc(&d.colidx, sizeof(int32_t) * std::max<int64_t>(d.nnz, 1)));
-    KR_CUDA(cudaMalloc(&d.vals, sizeof(C2<T>) * std::max<int64_t>(d.nnz, 1)));
+    KR_CUDA(cudaMalloc(&d.rowptr, sizeof(int64_t) * (n + 1) + kCsrPad));
+    KR_CUDA(cudaMalloc(&d.colidx, sizeof(int32_t) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
+    KR_CUDA(cudaMalloc(&d.vals, sizeof(C2<T>) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
+    for (int64_t i = 0; i < n; ++i) d.maxrow = std::max<int64_t>(d.maxrow, rp[i + 1] - rp[i]);
     KR_CUDA(cudaMemcpy(d.rowptr, rp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
     KR_CUDA(cudaMemcpy(d.colidx, ci.data(), sizeof(int32_t) * d.nnz, cudaMemcpyHostToDevice));
     KR_CUDA(cudaMemcpy(d.vals, hv.data(), sizeof(C2<T>) * d.nnz, cudaMemcpyHostToDevice));
@@ -179,10 +181,11 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
     orp[i + 1] = (int64_t)oci.size();
   }
   d.nnz = orp[n];
-  KR_CUDA(cudaMalloc(&d.rowptr, sizeof(int64_t) * (n + 1)));
-  KR_CUDA(cudaMalloc(&d.colidx, sizeof(int32_t) * std::max<int64_t>(d.nnz, 1)));
-  KR_CUDA(cudaMalloc(&d.offr, sizeof(T) * std::max<int64_t>(d.nnz, 1)));
-  KR_CUDA(cudaMalloc(&d.diag, sizeof(C2<T>) * n));
+  for (int64_t i = 0; i < n; ++i) d.maxrow = std::max<int64_t>(d.maxrow, orp[i + 1] - orp[i]);
+  KR_CUDA(cudaMalloc(&d.rowptr, sizeof(int64_t) * (n + 1) + kCsrPad));
+  KR_CUDA(cudaMalloc(&d.colidx, sizeof(int32_t) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
+  KR_CUDA(cudaMalloc(&d.offr, sizeof(T) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
+  KR_CUDA(cudaMalloc(&d.diag, sizeof(C2<T>) * n + kCsrPad));
   KR_CUDA(cudaMemcpy(d.rowptr, orp.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
   if (d.nnz) {
     KR_CUDA(cudaMemcpy(d.colidx, oci.data(), sizeof(int32_t) * d.nnz, cudaMemcpyHostToDevice));
@@ -367,6 +370,7 @@ struct Lin {
     t.coef_idx = (c.kind == COEF_MAT || c.kind == COEF_DIAG) ? matidx(c.p, c.kind == COEF_DIAG, mneg) : 0;
   }
   void blk(int o, const void* src, const Cf& c = Cf{}) { term(o, SRC_BLOCK, src, 0, c); }
+  void product(int o, const Cf& c = Cf{}) { term(o, SRC_SPMM, nullptr, 0, c); }  // (op(A) V)[j], see lin_product
   void vec(int o, const void* src, const Cf& c = Cf{}) { term(o, SRC_VEC, src, 0, c); }
   void reg(int o, int r, const Cf& c = Cf{}) { term(o, SRC_REG, nullptr, r, c); }
 };
@@ -520,6 +524,32 @@ struct Engine {
     return off;
   }
 
+  // Row-local combination L whose SRC_SPMM terms are the product op(A) V (op(A) = A or A^H).  The
+  // product is formed in the same pass (never stored) when the operator allows it -- CSR or
+  // stencil storage, no preconditioner, at most one fused Gram -- and fused products are on;
+  // otherwise it is stored in `scratch` first and the terms read it.  Both give the same values:
+  // every product kernel forms each entry with the same operations in the same order.
+  int lin_product(Lin& L, bool adjA, const void* V, void* scratch, Reds r = Reds{}) {
+    const bool fuse = fused_products_enabled() && !prec && !op.lat.on && count_grams(r.rs) <= 1 &&
+                      ng_capacity(threads_per_row(s)) >= count_grams(r.rs);
+    if (fuse) {
+      SpmmArgs<T> sp = op_spmm_args<T>(op, adjA != swap, s);
+      sp.n = n;
+      sp.V = reinterpret_cast<const C2<T>*>(V);
+      r.rs.partials = ws.partials;
+      const int grid = launch_lincomb_spmm<T>(L.a, r.rs, sp, row_grid(n, s), done(), st);
+      return reduce(r, grid);
+    }
+    spmm(adjA, s, V, scratch);
+    for (int o = 0; o < L.a.nout; ++o)
+      for (int t = 0; t < L.a.o[o].nterm; ++t)
+        if (L.a.o[o].t[t].src_kind == SRC_SPMM) {
+          L.a.o[o].t[t].src_kind = SRC_BLOCK;
+          L.a.o[o].t[t].src = scratch;
+        }
+    return lin(L, r);
+  }
+
   // U^H Y (n x sdim blocks in memory) -> dst (sdim^2 entries), any sdim <= 32
   void gram_from_memory(const void* U, const void* Y, int sdim, double2* dst) {
     const int grid0 = row_grid(n, sdim);
@@ -645,6 +675,66 @@ void make_shadow(Engine<T>& E, const void* R, void* Rh, int mode, const void* us
   E.lin(L);
 }
 
+// Gl-BiCG (Algorithm 2) with alpha from the adjoint product and the update fused with the
+// product: tr(Ph^H A P) = tr(Qh^H P) with Qh = A^H Ph, so alpha's denominator is a reduction of the
+// direction update of P, and X += alpha P, R -= alpha A P (formed in the pass, not stored),
+// Rh -= conj(alpha) Qh run in one pass.  Per iteration 2M + 17 Bv instead of 2M + 19 Bv; the
+// iterates equal Algorithm 2's in exact arithmetic.
+template <typename T>
+void run_gl_bicg_fused(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
+  Engine<T>& E = c.E;
+  void *R = E.blk(0), *Rh = E.blk(1), *P = E.blk(2), *Ph = E.blk(3), *Q = E.blk(4), *Qh = E.blk(5);
+  init_residual(E, c.B, c.X, R);
+  make_shadow(E, R, Rh, c.shadow_mode, c.shadow);
+  {
+    Lin L(E.n, E.s);
+    const int op_ = L.out(P), oph = L.out(Ph);
+    L.blk(op_, R);
+    L.blk(oph, Rh);
+    Reds r;
+    const int sl = r.add(RED_TRACE, op_, oph, nullptr, E.s);  // tr(Rh^H R)
+    const int off = E.lin(L, r);
+    E.coef(PH_SC_RHO0, off + sl);
+  }
+  {
+    Reds r;
+    const int sl = r.add(RED_TRACE, 0, -1, P, E.s);  // tr(P^H Qh) = conj(tr(Qh^H P))
+    const int off = E.spmm(true, E.s, Ph, Qh, r);
+    E.coef(PH_SC_ALPHA_CONJ, off + sl);
+  }
+  for (int it = 0; it < maxit; ++it) {
+    E.red_top = 0;
+    Lin L(E.n, E.s);
+    const int ox = L.out(c.X), orr = L.out(R), orh = L.out(Rh);
+    L.blk(ox, c.X);
+    L.blk(ox, P, sc(E.slot(SL_ALPHA)));
+    L.blk(orr, R);
+    L.product(orr, sc(E.slot(SL_ALPHA), false, true));
+    L.blk(orh, Rh);
+    L.blk(orh, Qh, sc(E.slot(SL_ALPHA), true, true));
+    Reds r2;
+    const int s2 = r2.add(RED_TRACE, orr, orh, nullptr, E.s);  // tr(Rh^H R)
+    const int s3 = r2.add(RED_NORM2, orr, -1, nullptr, E.s);
+    const int o2 = E.lin_product(L, false, P, Q, r2);
+    E.coef(PH_SC_BETA, o2 + s2, o2 + s3);
+    if (poll(it + 1)) break;
+    Lin Uh(E.n, E.s);
+    const int oph = Uh.out(Ph);
+    Uh.blk(oph, Rh);
+    Uh.blk(oph, Ph, sc(E.slot(SL_BETA), true));
+    E.lin(Uh);
+    E.spmm(true, E.s, Ph, Qh);
+    Lin U(E.n, E.s);
+    const int op_ = U.out(P);
+    U.blk(op_, R);
+    U.blk(op_, P, sc(E.slot(SL_BETA)));
+    Reds r1;
+    const int s1 = r1.add(RED_TRACE, op_, -1, Qh, E.s);  // tr(Qh^H P)
+    const int o1 = E.lin(U, r1);
+    E.coef(PH_SC_ALPHA, o1 + s1);
+  }
+}
+
 template <typename T>
 void run_gl_bicg(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
   Engine<T>& E = c.E;
@@ -688,6 +778,91 @@ void run_gl_bicg(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
     U.blk(oph, Ph, sc(E.slot(SL_BETA), true));
     E.lin(U);
     if (poll(it + 1)) break;
+  }
+}
+
+// eGl-BiCG (Algorithm 4) with the coefficient alpha taken from the adjoint product and the update
+// fused with the product.  sum(ph^H A P) = sum((A^H ph)^H P) = sum(qh^H P) with qh = A^H ph, so
+// after the n-vector product qh the denominator of alpha is a reduction of the direction update
+// P = R + beta P itself, and X += alpha P, R -= alpha A P, rh -= conj(alpha) qh run in one pass
+// that forms A P row by row without storing it.  Per iteration 2M + 8 Bv instead of 2M + 11 Bv
+// (M: one read of A; Bv: one n x s block); the iterates equal Algorithm 4's in exact arithmetic.
+template <typename T>
+void run_egl_bicg_fused(Ctx<T>& c, int maxit, const std::function<bool(int)>& poll) {
+  Engine<T>& E = c.E;
+  void *R = E.blk(0), *P = E.blk(1), *Q = E.blk(2);
+  void *rh = E.vecp(0), *ph = E.vecp(1), *qh = E.vecp(2);
+  init_residual(E, c.B, c.X, R);
+  E.coef(PH_FILL_ONES);
+  {
+    Lin L(E.n, E.s);
+    const int orh = L.out(rh, true);
+    if (c.shadow_mode == 2) L.vec(orh, c.shadow);
+    else L.blk(orh, R, mat(E.slot(SL_ONES)));  // mean of the columns of R_0 (Sec. 5)
+    E.lin(L);
+    if (c.shadow_mode == 1) {  // conj(mean)
+      Lin L2(E.n, 1);
+      const int o2 = L2.out(rh, true);
+      L2.vec(o2, rh, conjx());
+      E.lin(L2);
+    }
+  }
+  {
+    Lin L(E.n, E.s);
+    const int op_ = L.out(P);
+    L.blk(op_, R);
+    Reds r;
+    const int sl = r.add(RED_SUMV, op_, -1, rh, E.s);  // rho_0 = sum(rh^H R)
+    const int off = E.lin(L, r);
+    E.coef(PH_SC_RHO0, off + sl);
+    Lin V(E.n, 1);
+    const int ov = V.out(ph, true);
+    V.vec(ov, rh);
+    E.lin(V);
+  }
+  // alpha_0 = rho_0 / sum(qh^H P) with qh = A^H ph
+  E.spmm(true, 1, ph, qh);
+  {
+    Lin L(E.n, E.s);
+    const int o = L.out(nullptr);
+    L.blk(o, P);
+    Reds r;
+    const int sl = r.add(RED_SUMV, o, -1, qh, E.s);
+    const int off = E.lin(L, r);
+    E.coef(PH_SC_ALPHA, off + sl);
+  }
+  for (int it = 0; it < maxit; ++it) {
+    E.red_top = 0;
+    // X += alpha P; R -= alpha A P (formed in this pass); rh -= conj(alpha) qh; rho = sum(rh^H R), ||R||^2
+    Lin L(E.n, E.s);
+    const int ox = L.out(c.X), orr = L.out(R), orh = L.out(rh, true);
+    L.blk(ox, c.X);
+    L.blk(ox, P, sc(E.slot(SL_ALPHA)));
+    L.blk(orr, R);
+    L.product(orr, sc(E.slot(SL_ALPHA), false, true));
+    L.vec(orh, rh);
+    L.vec(orh, qh, sc(E.slot(SL_ALPHA), true, true));
+    Reds r2;
+    const int s2 = r2.add(RED_SUMV, orr, orh, nullptr, E.s);
+    const int s3 = r2.add(RED_NORM2, orr, -1, nullptr, E.s);
+    const int o2 = E.lin_product(L, false, P, Q, r2);
+    E.coef(PH_SC_BETA, o2 + s2, o2 + s3);
+    if (poll(it + 1)) break;
+    // ph = rh + conj(beta) ph; qh = A^H ph; P = R + beta P with alpha's denominator sum(qh^H P)
+    Lin Uv(E.n, 1);
+    const int ov = Uv.out(ph, true);
+    Uv.vec(ov, rh);
+    Uv.vec(ov, ph, sc(E.slot(SL_BETA), true));
+    E.lin(Uv);
+    E.spmm(true, 1, ph, qh);
+    Lin U(E.n, E.s);
+    const int op_ = U.out(P);
+    U.blk(op_, R);
+    U.blk(op_, P, sc(E.slot(SL_BETA)));
+    Reds r1;
+    const int s1 = r1.add(RED_SUMV, op_, -1, qh, E.s);
+    const int o1 = E.lin(U, r1);
+    E.coef(PH_SC_ALPHA, o1 + s1);
   }
 }
 
@@ -1436,7 +1611,7 @@ int blocks_needed(int method) {
   }
 }
 int vecs_needed(int method) {
-  if (method == KRM_EGL_BICG) return 2;
+  if (method == KRM_EGL_BICG) return 3;
   if (method == KRM_EGL_QMR) return 4;
   return 0;
 }
@@ -1537,8 +1712,14 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
   };
   Ctx<T> c{E, B, X, in.shadow, in.shadow_mode, 0};
   switch (method) {
-    case KRM_GL_BICG: run_gl_bicg<T>(c, in.maxit, poll); break;
-    case KRM_EGL_BICG: run_egl_bicg<T>(c, in.maxit, poll); break;
+    case KRM_GL_BICG:
+      if (fused_products_enabled()) run_gl_bicg_fused<T>(c, in.maxit, poll);
+      else run_gl_bicg<T>(c, in.maxit, poll);
+      break;
+    case KRM_EGL_BICG:
+      if (fused_products_enabled()) run_egl_bicg_fused<T>(c, in.maxit, poll);
+      else run_egl_bicg<T>(c, in.maxit, poll);
+      break;
     case KRM_LI_BICG: run_li_bicg<T>(c, in.maxit, poll); break;
     case KRM_LI_BICGSTAB: run_li_bicgstab<T>(c, in.maxit, poll); break;
     case KRM_LI_QMR: run_li_qmr<T>(c, in.maxit, poll); break;
@@ -1596,9 +1777,20 @@ double orthonormal_rhs(Operator& op, int s, const void* B, const void* X, void**
   KR_CUDA(cudaMemcpyAsync(ws.st, &h, sizeof(DevState), cudaMemcpyHostToDevice, st));
   standalone_qr(op, ws, op.n, s, *Q, st);
   DevState back{};
+  std::vector<double2> S((size_t)s * s);
   KR_CUDA(cudaMemcpyAsync(&back, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  KR_CUDA(cudaMemcpyAsync(S.data(), ws.arena + (size_t)SL_QR_S * kSlotElems, sizeof(double2) * s * s,
+                          cudaMemcpyDeviceToHost, st));
   KR_CUDA(cudaStreamSynchronize(st));
-  return (back.done && back.status == 1) ? -1.0 : res0;
+  if (back.done && back.status == 1) return -1.0;
+  // numerically rank deficient when a diagonal entry of S is at most 64 eps ||S||_F (the
+  // breakdown rule of the s x s solves): CholQR2's shifted first pass still returns a factor
+  double fro = 0.0, dmin = HUGE_VAL;
+  for (int i = 0; i < s; ++i)
+    for (int k = 0; k < s; ++k) fro += S[(size_t)i * s + k].x * S[(size_t)i * s + k].x + S[(size_t)i * s + k].y * S[(size_t)i * s + k].y;
+  for (int i = 0; i < s; ++i) dmin = std::min(dmin, std::hypot(S[(size_t)i * s + i].x, S[(size_t)i * s + i].y));
+  if (!(dmin > 64.0 * 2.220446049250313e-16 * std::sqrt(fro))) return -1.0;
+  return res0;
 }
 
 // X += Y S with Y and S from the last orthonormal_rhs on this operator and s
