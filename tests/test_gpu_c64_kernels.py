@@ -6,11 +6,12 @@ compared with the FP64 oracle evaluated on the complex64 inputs (A, V, U rounded
 to complex64 and widened back, so the only differences are the kernels' FP32
 roundings), with bounds from the standard error analysis of a sum of products.
 
-Both complex64 kernel variants are covered: one column per thread, and two
-adjacent columns per thread (kr_set_column_pairs).  The two compute every output
-entry with the same operations in the same order, so their products are compared
-bit for bit; their reductions group the partial sums differently and agree to FP32
-rounding.
+All three complex64 product kernels are covered: the row-tile kernel whose tiles are
+staged in shared memory by bulk asynchronous copies (kr_set_tile_kernels), two adjacent
+columns per thread (kr_set_column_pairs), and one column per thread.  They compute
+every output entry with the same operations in the same order, so their products are
+compared bit for bit; their reductions group the partial sums differently and agree to
+FP32 rounding.  After the tests no bounded device wait of the tile kernel has run out.
 """
 import numpy as np
 import pytest
@@ -34,8 +35,10 @@ def kr():
     build.build()
     import paper_1504_04395_gb300 as m
     m.load_library()
+    m.kr_take_device_timeouts(reset=True)
     yield m
     m.kr_set_column_pairs(True)
+    m.kr_set_tile_kernels(True)
 
 
 def c64(x):
@@ -52,11 +55,17 @@ def host(t):
 
 
 def with_pairs(kr, on, fn):
-    kr.kr_set_column_pairs(on)
+    """on: True = column pairs (tile kernel off), False = one column (tile kernel off), "tile" = default."""
+    kr.kr_set_tile_kernels(on == "tile")
+    kr.kr_set_column_pairs(on is not False)
     try:
         return fn()
     finally:
         kr.kr_set_column_pairs(True)
+        kr.kr_set_tile_kernels(True)
+
+
+VARIANTS = ("tile", True, False)
 
 
 SIZES = [1, 7, 1000, 5003]
@@ -78,21 +87,19 @@ def test_c64_spmm_matches_oracle(kr, s, real_offdiag):
             ref = oracle.spmm(M, V)
             scale = abs(M) @ np.abs(V)
             outs = []
-            for pairs in (True, False):
+            for pairs in VARIANTS:
                 Y, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(op, Vd, adjoint=adj))
                 outs.append(Y)
                 # each entry: at most kmax + 1 complex products summed in FP32
                 err = np.abs(host(Y) - ref)
                 assert np.all(err <= 4 * (kmax + 2) * U32 * scale + 1e-30), (n, s, adj, pairs)
-            assert torch.equal(outs[0], outs[1]), (n, s, adj)
+            assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]), (n, s, adj)
         op.close()
 
 
 @pytest.mark.parametrize("s", [2, 4, 8, 16, 32])
 @pytest.mark.parametrize("kind", ["gram", "trace", "sumv", "norm2"])
 def test_c64_fused_reductions(kr, s, kind):
-    if kind == "gram" and s > 16:
-        pytest.skip("a fused s x s Gram is held in registers for s <= 16")
     n = 6007
     rp, ci, v = random_csr(n, seed=s)
     A = oracle.csr_matrix_from_arrays(n, rp, ci, c64(v))
@@ -101,9 +108,13 @@ def test_c64_fused_reductions(kr, s, kind):
     U = c64(gaussian_block(n, s, seed=2) if kind != "sumv" else gaussian_block(n, 1, seed=2)[:, 0])
     Ud = dev32(U) if kind != "norm2" else None
     res = {}
-    for pairs in (True, False):
+    # the per-thread kernels hold a fused s x s Gram in registers for s <= 16 only
+    variants = ("tile",) if (kind == "gram" and s > 16) else VARIANTS
+    for pairs in variants:
         res[pairs] = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(op, dev32(V), Ud, kind=kind))
-    assert torch.equal(res[True][0], res[False][0])
+    for pairs in variants[1:]:
+        assert torch.equal(res["tile"][0], res[pairs][0])
+    res.setdefault(True, res["tile"])
     Yk = host(res[True][0])  # the stored complex64 product
     if kind == "gram":
         ref = oracle.gram(U, Yk)
@@ -117,14 +128,14 @@ def test_c64_fused_reductions(kr, s, kind):
     else:
         ref = np.array([np.linalg.norm(Yk) ** 2])
         bound = ref.copy()
-    for pairs in (True, False):
+    for pairs in variants:
         got = host(res[pairs][1]).reshape(ref.shape)
         if kind == "norm2":
             got = got.real
         # FP32 partial sums of at most a few hundred terms per thread, then FP64
         assert np.all(np.abs(got - ref) <= 1e-4 * bound.reshape(ref.shape)), (kind, pairs)
     # the stand-alone complex64 reduction of the stored product agrees to FP32 rounding
-    for pairs in (True, False):
+    for pairs in (True, False) if not (kind == "gram" and s > 16) else ():
         out2 = with_pairs(kr, pairs, lambda: kr.kr_block_reduce_c64(Ud, res[True][0], kind=kind))
         got2 = host(out2).reshape(ref.shape)
         if kind == "norm2":
@@ -132,7 +143,7 @@ def test_c64_fused_reductions(kr, s, kind):
         assert np.all(np.abs(got2 - ref) <= 1e-4 * bound.reshape(ref.shape)), (kind, pairs)
     # fixed summation order: bitwise reproducible
     _, out3 = kr.kr_op_apply_reduce_c64(op, dev32(V), Ud, kind=kind)
-    assert torch.equal(out3, res[True][1])
+    assert torch.equal(out3, res["tile"][1])
     op.close()
 
 
@@ -146,7 +157,7 @@ def test_c64_stencil_equals_csr(kr, dims, s):
     st = kr.Operator.stencil(dims, centre, minus, plus)
     csr = kr.Operator(cd.n, rp, ci, v)
     Vd = dev32(gaussian_block(cd.n, s, seed=s))
-    for pairs in (True, False):
+    for pairs in VARIANTS:
         for adj in (False, True):
             Ys, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(st, Vd, adjoint=adj))
             Yc, _ = with_pairs(kr, pairs, lambda: kr.kr_op_apply_reduce_c64(csr, Vd, adjoint=adj))
@@ -167,7 +178,7 @@ def test_mixed_solve_with_and_without_pairs(kr, method):
     B = gaussian_block(cd.n, s, seed=7)
     A = oracle.csr_matrix_from_arrays(cd.n, rp, ci, v)
     X_lu = splu(A.tocsc()).solve(B)  # direct sparse LU: the exact solution to rounding
-    for pairs in (True, False):
+    for pairs in VARIANTS:
         X, info = with_pairs(kr, pairs, lambda: kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10,
                                                             maxit=2000, precision=kr.FP32_REFINE))
         assert info.status == "OK", (method, pairs, info)
@@ -202,3 +213,42 @@ def test_mixed_block_methods(kr, method):
     assert np.linalg.norm(B - A @ X) / np.linalg.norm(B) <= 1.01e-10
     assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
     op.close()
+
+
+@pytest.mark.parametrize("s", [4, 8, 16, 32])
+@pytest.mark.parametrize("kind", ["gram", "trace"])
+@pytest.mark.parametrize("adj", [False, True])
+def test_c64_tile_product_full_size(kr, s, kind, adj):
+    """128^3 convection-diffusion (the benchmark's matrix, 14.6M entries): the tile kernel's
+    product with a fused Gram or trace against FP64 on the host from the complex64 inputs, on
+    the rows of a seeded sample and in full for the reduction; products bitwise equal to the
+    column-pair kernel's."""
+    cd = ConvDiff((128, 128, 128), (0.8, 0.8, 0.8), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    n = cd.n
+    op = kr.Operator(n, rp, ci, v)
+    g = torch.Generator(device="cuda").manual_seed(s)
+    Vd = torch.randn(n, s, dtype=torch.complex64, device="cuda", generator=g)
+    Ud = torch.randn(n, s, dtype=torch.complex64, device="cuda", generator=g)
+    Y, out = kr.kr_op_apply_reduce_c64(op, Vd, Ud, kind=kind, adjoint=adj)
+    Yp, _ = with_pairs(kr, True, lambda: kr.kr_op_apply_reduce_c64(op, Vd, adjoint=adj))
+    assert torch.equal(Y, Yp)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, c64(v))
+    M = oracle.adjoint(A) if adj else A
+    V, U, Yh = host(Vd), host(Ud), host(Y)
+    rows = np.random.default_rng(s).integers(0, n, 3000)
+    Ms = M[rows]
+    ref = Ms @ V
+    scale = abs(Ms) @ np.abs(V)
+    assert np.all(np.abs(Yh[rows] - ref) <= 4 * 9 * U32 * scale)
+    if kind == "gram":
+        want, bound = U.conj().T @ Yh, np.abs(U).T @ np.abs(Yh)
+    else:
+        want, bound = np.array([np.sum(U.conj() * Yh)]), np.array([np.sum(np.abs(U) * np.abs(Yh))])
+    got = host(out).reshape(want.shape)
+    assert np.all(np.abs(got - want) <= 1e-4 * bound)
+    op.close()
+
+
+def test_no_device_wait_ran_out(kr):
+    assert kr.kr_take_device_timeouts(reset=False) == 0

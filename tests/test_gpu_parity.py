@@ -408,3 +408,94 @@ def test_create_csr_from_device_arrays(kr):
         kr.Operator.from_tensors(rpt, bad, vt)
     for o in (op, ref, host):
         o.close()
+
+
+@pytest.mark.parametrize("method", ["gl_bicg", "egl_bicg"])
+def test_fused_schedule_against_oracle_and_literal(kr, method):
+    """Gl-/eGl-BiCG with alpha from the adjoint product and the X / R update fused with A P
+    (kr_set_fused_products, the default) against the oracle's Algorithms 2 and 4 (the plain bar),
+    against the literal schedule of the same library, and the bytes each moves per iteration
+    (launch profile: 2M + 8 Bv instead of 2M + 11 Bv for eGl-BiCG)."""
+    n, rp, ci, v = conv(24, shift=0.3j)
+    B = gaussian_block(n, 4, seed=0)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    ref = oracle.solve(method, A, B, tol=1e-8, maxit=300)
+    op = kr.Operator(n, rp, ci, v)
+    runs = {}
+    for fused in (True, False):
+        kr.kr_set_fused_products(fused)
+        try:
+            runs[fused] = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-8, maxit=300)
+        finally:
+            kr.kr_set_fused_products(True)
+    (Xf, inf_f), (Xl, inf_l) = runs[True], runs[False]
+    check_history(ref.history, inf_f.history, sens=None, method=method, test="fused_schedule")
+    assert inf_f.status == "OK" and inf_f.iters == ref.iters == inf_l.iters
+    assert rel(Xf.cpu().numpy(), Xl.cpu().numpy()) < 1e-9
+    assert rel(Xf.cpu().numpy(), ref.X) < 1e-9
+    # bytes per iteration, from the launch profile of 10-iteration solves
+    per_iter = {}
+    for fused in (True, False):
+        kr.kr_set_fused_products(fused)
+        try:
+            for k in (5, 15):
+                kr.kr_profile_read(reset=True)
+                kr.kr_profile_enable(True, time_kernels=False)
+                kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=0.0, maxit=k, graphs="off")
+                prof = kr.kr_profile_read(reset=True)
+                kr.kr_profile_enable(False)
+                per_iter[(fused, k)] = sum(c["bytes"] for c in prof.values())
+        finally:
+            kr.kr_set_fused_products(True)
+    fused_b = (per_iter[(True, 15)] - per_iter[(True, 5)]) / 10
+    literal_b = (per_iter[(False, 15)] - per_iter[(False, 5)]) / 10
+    s = 4
+    Bv = 16.0 * n * s
+    saved = (literal_b - fused_b) / Bv
+    # eGl-BiCG: three blocks fewer, one n-vector (1/s of a block) more; Gl-BiCG: two blocks fewer
+    assert saved == pytest.approx(3.0 - 1.0 / s if method == "egl_bicg" else 2.0, abs=0.02), saved
+    op.close()
+
+
+@pytest.mark.parametrize("kind", ["stencil", "lattice", "ilu0", "mixed"])
+def test_fused_schedule_other_operators(kr, kind):
+    """The fused schedule on the matrix-free stencil (product formed in the pass), the matrix-free
+    lattice and the ILU(0)-preconditioned CSR operator (product stored first, then combined), and
+    in mixed precision (complex64 inner solves): eGl-BiCG against the oracle or dense LU."""
+    method = "egl_bicg"
+    if kind == "lattice":
+        from workloads import Lattice4D, lattice_csr
+        from workloads.lattice import GAMMA, LATTICE_MASS, haar_links
+        lat = Lattice4D((4, 4, 4, 4), LATTICE_MASS, seed=0)
+        links = haar_links(lat.dims, lat.seed)
+        rp, ci, v = lattice_csr(lat, links)
+        n = lat.n
+        op = kr.Operator.lattice4d(lat.dims, 4.0 + LATTICE_MASS, -0.5, GAMMA, links)
+    else:
+        cd = ConvDiff((10, 10, 10), (0.4, 0.4, 0.4), 0.3j)
+        rp, ci, v = convdiff_csr(cd)
+        n = cd.n
+        if kind == "stencil":
+            centre, minus, plus = cd.coefficients()
+            op = kr.Operator.stencil(cd.dims, centre, minus, plus)
+        else:
+            op = kr.Operator(n, rp, ci, v)
+            if kind == "ilu0":
+                op.set_preconditioner("ilu0")
+    B = gaussian_block(n, 4, seed=3)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    if kind == "mixed":
+        X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=1000,
+                              precision=kr.FP32_REFINE)
+        assert info.status == "OK" and info.fp64_iters == 0, info
+        assert rel(X.cpu().numpy(), np.linalg.solve(A.toarray(), B)) < 1e-8
+    elif kind == "ilu0":
+        X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=500)
+        assert info.status == "OK"
+        assert rel(X.cpu().numpy(), np.linalg.solve(A.toarray(), B)) < 1e-8
+    else:
+        ref = oracle.solve(method, A, B, tol=1e-10, maxit=1000)
+        X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=1000)
+        assert info.status == "OK" and abs(info.iters - ref.iters) <= 1
+        check_history(ref.history, info.history, sens=None, method=method, test="fused_" + kind)
+    op.close()
