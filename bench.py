@@ -81,6 +81,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-iters", type=int, default=5)
     ap.add_argument("--spec", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--config2-sweep", action="store_true",
+                    help="time to 1e-8 of every method on the 128^3 workload for s in {1, 4, 8, 16}")
     ap.add_argument("--config5", action="store_true",
                     help="differentiation: forward eGl-BiCG + adjoint solve + gradient on 3D convection-diffusion "
                          "64^3 with learnable Peclet numbers, s = 16; gradient checked against finite differences")
@@ -717,6 +719,8 @@ def config4(args):
     hbm_peak, _ = measured_peaks()
     out = {"workload": "4D lattice %d^4 x 12 (n=%d, nnz=%d), m=%.2f, s=%d Gaussian RHS, eGl-BiCG to 1e-10, %s operator"
                        % (L, lat.n, nnz, LATTICE_MASS, s, "matrix-free" if args.operator == "lattice" else "CSR"),
+           "mass_reading": "diagonal 4 + m with m = %.2f, the spectrum kept in the right half-plane as the paper "
+                           "states for Example 4 (kappa about 54 on 4^4) rather than kappa = 1e3" % LATTICE_MASS,
            "generation_s": gen_s}
     X = {}
     for prec, name in ((kr.FP64, "fp64"), (kr.FP32_REFINE, "fp32_refine")):
@@ -865,6 +869,13 @@ def config3(args):
     shadow_blk = torch.from_numpy(gaussian_block(lat.n, 12, seed=5)).cuda()
     out = {"workload": "4D lattice %d^4 x 12 (n=%d), m=%.2f, s=12, to 1e-8, %s operator"
                        % (L, lat.n, LATTICE_MASS, "matrix-free" if args.operator == "lattice" else "CSR"),
+           "mass_reading": "diagonal 4 + m with m = %.2f, the spectrum kept in the right half-plane as the paper "
+                           "states for Example 4 (kappa about 54 on 4^4); a mass giving kappa = 1e3 puts eigenvalues "
+                           "in the left half-plane, where all three methods diverge on 16^4" % LATTICE_MASS,
+           "shadow_reading": "point sources (the 12 unit vectors of one site): seeded Gaussian shadows (a vector for "
+                             "the economic methods, a 12-column block for Bl-BiCGStab-rQ), since the default shadows "
+                             "make the first inner products cancel to rounding noise; Gaussian right-hand sides: the "
+                             "paper's defaults (R0, the mean of R0's columns)",
            "results": {}}
     for kind, B in rhs.items():
         Bd = torch.from_numpy(B).cuda()
@@ -938,8 +949,75 @@ def spmm_rates(args):
         kr.kr_set_tile_kernels(True)
         kr.kr_set_column_pairs(True)
         del V, U, Y
+    # the same operator without stored matrix (the 7-point stencil formed from its coefficients):
+    # algorithmic bytes are V and U read and Y written
+    centre, minus, plus = op.coefficients()
+    St = kr.Operator.stencil(op.dims, centre, minus, plus)
+    g = torch.Generator(device="cuda").manual_seed(s)
+    V = torch.randn(n, s, dtype=torch.complex64, device="cuda", generator=g)
+    U = torch.randn(n, s, dtype=torch.complex64, device="cuda", generator=g)
+    Y = torch.empty_like(V)
+    byts = 3 * 8 * n * s
+    for kind in ("gram", "trace"):
+        for vname, (tile, pairs) in (("tile", (True, True)), ("pairs", (False, True))):
+            if kind == "gram" and s > 16 and not tile:
+                continue
+            kr.kr_set_tile_kernels(tile)
+            kr.kr_set_column_pairs(pairs)
+            for _ in range(5):
+                kr.kr_op_apply_reduce_c64(St, V, U, kind=kind, Y=Y)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(30):
+                kr.kr_op_apply_reduce_c64(St, V, U, kind=kind, Y=Y)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 30
+            gbs = byts / ms / 1e6
+            out["rates"]["stencil_c64_%s_%s" % (kind, vname)] = {"ms": ms, "bytes": byts, "gbs": gbs,
+                                                               "hbm_frac": gbs / hbm_peak}
+    kr.kr_set_tile_kernels(True)
+    kr.kr_set_column_pairs(True)
+    St.close()
     out["device_wait_timeouts"] = kr.kr_take_device_timeouts(reset=True)
     print(json.dumps(out))
+
+
+def config2_sweep(args):
+    """Config 2 across block widths: 3D convection-diffusion --grid^3 (default 128^3), Pe 0.8, shift
+    0.05i, s in {1, 4, 8, 16} Gaussian right-hand sides (seed 0), X0 = 0; every method solves to 1e-8
+    (maxit --maxit), FP64; per method and s: status, iterations, time to tolerance (CUDA events around
+    kr_solve after one untimed solve that allocates the workspaces) and RHS*iterations/s."""
+    import torch
+    from paper_1504_04395_gb300 import build
+    build.build()
+    import paper_1504_04395_gb300 as kr
+    methods = args.methods.split(",") if args.methods else list(METHODS10)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "config2_sweep", "tol": args.tol, "maxit": args.maxit, "results": {}}
+    op = None
+    for s in (1, 4, 8, 16):
+        op_, rp, ci, v, B = workload(args.grid, s)
+        if op is None:
+            op = kr.Operator(op_.n, rp, ci, v)
+            out["workload"] = workload_name(args.grid, s, op_.n, len(ci)).replace("s=%d " % s, "")
+        Bd = torch.from_numpy(B).cuda()
+        Xd = torch.zeros_like(Bd)
+        row = {}
+        for m in methods:
+            kr.kr_solve(op, m, Bd, torch.zeros_like(Bd), tol=args.tol, maxit=2)  # workspaces
+            info, ms = solve_timed(kr, torch, op, m, Bd, Xd, args.tol, args.maxit, stream)
+            row[m] = {"status": info.status, "iters": info.iters, "relres_true": info.relres_true,
+                      "time_to_tol_ms": ms if info.status == "OK" else None, "ms_to_exit": ms,
+                      "rhs_iters_per_s": s * info.iters / (ms / 1000.0)}
+            if info.status == "BREAKDOWN":
+                row[m]["breakdown_iter"] = info.breakdown_iter
+        out["results"]["s%d" % s] = row
+        del Bd, Xd
+    print(json.dumps(out))
+    op.close()
 
 
 def config5(args):
@@ -1062,6 +1140,9 @@ def main():
         return
     if args.config5:
         config5(args)
+        return
+    if args.config2_sweep:
+        config2_sweep(args)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -209,12 +209,13 @@ inline int round16i(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
 // Shared-memory layout and reduction maps of a tile launch; false when the launch does not fit
 // the tile kernel (then the other kernels run it).
 static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L) {
-  if (a.nst > 0 || a.lat) return false;
+  if (a.lat) return false;
+  const bool sten = a.nst > 0;
   const int s = a.s;
   if (s != 4 && s != 8 && s != 16 && s != 32) return false;
   const int GP = s / 2;
   const int R = std::min(128, kTileThreadsMax / GP);
-  if ((int64_t)R * a.maxrow > kTileEcap) return false;
+  if (!sten && (int64_t)R * a.maxrow > kTileEcap) return false;
   if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
   if (rs.nred > kMaxRed) return false;
   L = TileLayout{};
@@ -252,25 +253,23 @@ static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& 
   L.ngram = ngram;
   L.ystage = ngram > 0 ? 1 : 0;
   L.ncompact = nc;
-  const bool split = a.split != 0;
+  const bool split = !sten && a.split != 0;
+  L.mode = sten ? 2 : (split ? 1 : 0);
   L.off_rp = 0;
-  L.sz_rp = round16i((int64_t)(R + 2) * 8);
+  L.sz_rp = sten ? 0 : round16i((int64_t)(R + 2) * 8);
   L.off_dg = L.sz_rp;
   L.sz_dg = split ? R * 8 : 0;
   L.off_u = L.sz_rp + L.sz_dg;
   L.sz_u = R * s * 8;
   L.off_col = 0;
-  L.sz_col = round16i((int64_t)(kTileEcap + 8) * 4);
+  L.sz_col = sten ? 0 : round16i((int64_t)(kTileEcap + 8) * 4);
   L.off_val = L.sz_col;
-  L.sz_val = round16i((int64_t)(kTileEcap + 8) * (split ? 4 : 8));
+  L.sz_val = sten ? 0 : round16i((int64_t)(kTileEcap + 8) * (split ? 4 : 8));
   const int strideA = L.sz_rp + L.sz_dg + L.nu * L.sz_u, strideB = L.sz_col + L.sz_val;
   L.off_y = kTileStagesA * strideA + kTileStagesB * strideB;
   const int staged = L.off_y + (L.ystage ? R * s * 8 : 0);
   const int T = GP * R;
-  // Gram records: per (warp, row group of the warp) for s <= 16, per row group of the CTA for s = 32
-  const int nb = GP * GP;
-  const int nrec = GP <= 8 ? (T / 32) * (nb < 32 ? 32 / nb : 1) : T / nb;
-  const int final_red = (T / 32) * nc * 8 + ngram * nrec * s * s * 8;
+  const int final_red = (T / 32) * nc * 8 + ngram * (T / (GP * GP)) * s * s * 8;
   L.total = std::max(staged, final_red);
   return L.total <= kMaxDynSmem;
 }

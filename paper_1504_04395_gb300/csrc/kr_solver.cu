@@ -833,17 +833,22 @@ void run_egl_bicg_fused(Ctx<T>& c, int maxit, const std::function<bool(int)>& po
   }
   for (int it = 0; it < maxit; ++it) {
     E.red_top = 0;
-    // X += alpha P; R -= alpha A P (formed in this pass); rh -= conj(alpha) qh; rho = sum(rh^H R), ||R||^2
+    // rh -= conj(alpha) qh (an n-vector, its own launch: the block pass then has block outputs
+    // only and runs on column pairs in complex64)
+    Lin Lv(E.n, 1);
+    const int orh = Lv.out(rh, true);
+    Lv.vec(orh, rh);
+    Lv.vec(orh, qh, sc(E.slot(SL_ALPHA), true, true));
+    E.lin(Lv);
+    // X += alpha P; R -= alpha A P (formed in this pass); rho = sum(rh^H R), ||R||^2
     Lin L(E.n, E.s);
-    const int ox = L.out(c.X), orr = L.out(R), orh = L.out(rh, true);
+    const int ox = L.out(c.X), orr = L.out(R);
     L.blk(ox, c.X);
     L.blk(ox, P, sc(E.slot(SL_ALPHA)));
     L.blk(orr, R);
     L.product(orr, sc(E.slot(SL_ALPHA), false, true));
-    L.vec(orh, rh);
-    L.vec(orh, qh, sc(E.slot(SL_ALPHA), true, true));
     Reds r2;
-    const int s2 = r2.add(RED_SUMV, orr, orh, nullptr, E.s);
+    const int s2 = r2.add(RED_SUMV, orr, -1, rh, E.s);
     const int s3 = r2.add(RED_NORM2, orr, -1, nullptr, E.s);
     const int o2 = E.lin_product(L, false, P, Q, r2);
     E.coef(PH_SC_BETA, o2 + s2, o2 + s3);

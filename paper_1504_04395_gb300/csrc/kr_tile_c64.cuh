@@ -86,31 +86,34 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ uint32_t round16(uint64_t b) { return (uint32_t)((b + 15) & ~(uint64_t)15); }
 
-template <int GP, bool SPLIT>
+// operator storage of a tile launch
+enum TileMode : int { TILE_CSR = 0, TILE_SPLIT = 1, TILE_STENCIL = 2 };
+
+template <int GP, int MODE>
 struct TileKernel {
   static constexpr int S = 2 * GP;           // columns
   static constexpr int NB = GP * GP;         // 2 x 2 Gram blocks
+  static constexpr bool SPLIT = MODE == TILE_SPLIT;
+  static constexpr bool STEN = MODE == TILE_STENCIL;
 
-  // A-stage copies of tile t into stage `st`: row pointers, diagonal, U operands
+  // A-stage copies of a tile into stage `sm`: row pointers and diagonal (CSR), U operands; and a
+  // bulk L2 prefetch of the tile's rows of V
   static __device__ void issue_a(const SpmmArgs<float>& a, const TileLayout& L, unsigned char* sm, uint64_t* bar,
                                  int64_t r0, int rows) {
-    const uint32_t brp = round16((uint64_t)(rows + 1) * 8);
-    uint32_t total = brp;
+    const uint32_t brp = STEN ? 0 : round16((uint64_t)(rows + 1) * 8);
     const uint32_t bdg = SPLIT ? round16((uint64_t)rows * 8) : 0;
-    total += bdg;
     const uint32_t bu = (uint32_t)rows * S * 8;  // a multiple of 16 (S even)
-    total += bu * L.nu;
-    mbar_arrive_expect(bar, total);
+    mbar_arrive_expect(bar, brp + bdg + bu * L.nu);
     // the tile's own rows of V into L2 (gathered by its diagonal and by the neighbouring tiles'
     // rows, which other CTAs process at about the same time): one instruction, no completion
     prefetch_l2_bulk(reinterpret_cast<const float2*>(a.V) + r0 * S, bu);
-    bulk_load(sm + L.off_rp, a.rowptr + r0, brp, bar);
+    if (!STEN) bulk_load(sm + L.off_rp, a.rowptr + r0, brp, bar);
     if (SPLIT) bulk_load(sm + L.off_dg, a.diag + r0, bdg, bar);
     for (int u = 0; u < L.nu; ++u)
       bulk_load(sm + L.off_u + u * L.sz_u, reinterpret_cast<const float2*>(L.U[u]) + r0 * S, bu, bar);
   }
 
-  // B-stage copies: the tile's entries [k0 & ~3, k1), read from the staged row pointers
+  // B-stage copies (CSR): the tile's entries [k0 & ~3, k1), read from the staged row pointers
   static __device__ void issue_b(const SpmmArgs<float>& a, const TileLayout& L, unsigned char* sm_b,
                                  const int64_t* rp, uint64_t* bar, int rows) {
     const int64_t k0 = rp[0] & ~(int64_t)3, k1 = rp[rows];
@@ -150,87 +153,44 @@ __device__ __forceinline__ void gram_stage_block(float2* G, int a0, int c0, floa
   G[(a0 + 1) * S + c0 + 1] = x11;
 }
 
-// bounded wait that also gives up once another thread of the CTA has given up (abort)
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (unsigned i = 0; i < kWaitPolls; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (i >= 32) __nanosleep(200);
-  }
-  return false;
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
-// Gram blocks of one warp (s <= 16): the warp's own rows of the tile, U from the staged tile and
-// Y from the rows this warp just wrote; lane -> WBLK 2 x 2 blocks for one row group of the warp.
-template <int S, int WBLK>
-__device__ __forceinline__ void warp_gram(const float2* Us, const float2* Yt, int r_lo, int r_hi, int lane,
-                                          float2 (&g)[WBLK * 4]) {
-  constexpr int GP = S / 2;
-  constexpr int NB = GP * GP;
-  constexpr int NBL = NB < 32 ? NB : 32;    // blocks covered by one row group of lanes
-  constexpr int RGW = NB < 32 ? 32 / NB : 1;  // row groups per warp
-  const int grp = lane / NBL, bl = lane % NBL;
-  const int span = (r_hi - r_lo + RGW - 1) / RGW;
-  const int q0 = r_lo + grp * span, q1 = min(r_hi, q0 + span);
+// y += sum over the batch's m entries of val[k + u] * x[u] (real values for the split storage)
+template <bool SPLIT, int NBATCH>
+__device__ __forceinline__ void tile_fma(const unsigned char* valbuf, int k, int m, const Pair (&x)[NBATCH], Pair& y) {
+  if constexpr (SPLIT) {
+    const float* val = reinterpret_cast<const float*>(valbuf);
 #pragma unroll
-  for (int k = 0; k < WBLK; ++k) {
-    const int b = bl + 32 * k;
-    const int a0 = 2 * (b / GP), c0 = 2 * (b % GP);
-    float2 x00 = g[4 * k], x01 = g[4 * k + 1], x10 = g[4 * k + 2], x11 = g[4 * k + 3];
-    for (int r = q0; r < q1; ++r) {
-      const float4 u = *reinterpret_cast<const float4*>(Us + r * S + a0);
-      const float4 y = *reinterpret_cast<const float4*>(Yt + r * S + c0);
-      const float2 ua = make_float2(u.x, u.y), ub = make_float2(u.z, u.w);
-      const float2 ya = make_float2(y.x, y.y), yb = make_float2(y.z, y.w);
-      x00 = cfmaconj<float>(ua, ya, x00);
-      x01 = cfmaconj<float>(ua, yb, x01);
-      x10 = cfmaconj<float>(ub, ya, x10);
-      x11 = cfmaconj<float>(ub, yb, x11);
-    }
-    g[4 * k] = x00; g[4 * k + 1] = x01; g[4 * k + 2] = x10; g[4 * k + 3] = x11;
-  }
-}
-
-template <int S, int WBLK>
-__device__ __forceinline__ void warp_gram_stage(float2* G, int lane, const float2 (&g)[WBLK * 4]) {
-  constexpr int GP = S / 2;
-  constexpr int NB = GP * GP;
-  constexpr int NBL = NB < 32 ? NB : 32;
-  const int grp = lane / NBL, bl = lane % NBL;
-  float2* Gg = G + (size_t)grp * S * S;
+    for (int u = 0; u < NBATCH; ++u)
+      if (u < m) {
+        y.a = cfmareal<float>(val[k + u], x[u].a, y.a);
+        y.b = cfmareal<float>(val[k + u], x[u].b, y.b);
+      }
+  } else {
+    const float2* val = reinterpret_cast<const float2*>(valbuf);
 #pragma unroll
-  for (int k = 0; k < WBLK; ++k) {
-    const int b = bl + 32 * k;
-    gram_stage_block<S>(Gg, 2 * (b / GP), 2 * (b % GP), g[4 * k], g[4 * k + 1], g[4 * k + 2], g[4 * k + 3]);
+    for (int u = 0; u < NBATCH; ++u)
+      if (u < m) {
+        y.a = cfma<float>(val[k + u], x[u].a, y.a);
+        y.b = cfma<float>(val[k + u], x[u].b, y.b);
+      }
   }
 }
 
-// NG: fused Grams (0..2); at most kTileRowReds per-row reductions.
-// s <= 16: each warp forms the Gram blocks of its own rows (no CTA barrier in the tile loop; the
-// stages are handed back to the producer through "empty" mbarriers that every warp arrives on);
-// s = 32: the Grams are formed by the whole CTA after a barrier (their s^2 accumulators per lane
-// would not fit a warp).
-template <int GP, bool SPLIT, int NG>
+// MODE: TileMode; NG: fused Grams (0..2); at most kTileRowReds per-row reductions.  The Grams are
+// formed by the whole CTA after each tile from the shared-memory copies of Y and U.
+template <int GP, int MODE, int NG>
 __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<float> a, RedSet rs, TileLayout L,
                                                                         const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
-  using K = TileKernel<GP, SPLIT>;
+  using K = TileKernel<GP, MODE>;
   constexpr int S = K::S;
   constexpr int NB = K::NB;
-  constexpr bool WG = GP <= 8;                 // Grams per warp
-  constexpr int RPW = 32 / GP;                 // rows per warp in the product phase
-  constexpr int WBLK = NB >= 32 ? NB / 32 : 1; // 2 x 2 blocks per lane (warp Grams)
-  constexpr int RGW = NB < 32 ? 32 / NB : 1;   // row groups per warp (warp Grams)
+  constexpr bool SPLIT = K::SPLIT, STEN = K::STEN;
   extern __shared__ __align__(128) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t fullA[kTileStagesA], fullB[kTileStagesB], emptyA[kTileStagesA],
-      emptyB[kTileStagesB];
-  __shared__ volatile int s_abort;
+  __shared__ __align__(8) uint64_t barA[kTileStagesA], barB[kTileStagesB];
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int T = blockDim.x;  // = GP * R
-  const int nw = T >> 5;
   const int R = L.R;
   const int64_t n = a.n;
   const int ntiles = (int)((n + R - 1) / R);
@@ -242,30 +202,37 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
   unsigned char* baseA = tsm;
   unsigned char* baseB = tsm + kTileStagesA * strideA;
   float2* Yt = reinterpret_cast<float2*>(tsm + L.off_y);
+  // stencil coefficients, converted once (double -> float runs on the FP64 pipe)
+  float2 stc = make_float2(0.f, 0.f), stm[3], stp[3];
+  if constexpr (STEN) {
+    stc = make_float2((float)a.sc.x, (float)a.sc.y);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      stm[q] = make_float2((float)a.sm[q].x, (float)a.sm[q].y);
+      stp[q] = make_float2((float)a.sp[q].x, (float)a.sp[q].y);
+    }
+  }
 
   if (tid == 0) {
-    for (int k = 0; k < kTileStagesA; ++k) { mbar_init(&fullA[k], 1); mbar_init(&emptyA[k], nw); }
-    for (int k = 0; k < kTileStagesB; ++k) { mbar_init(&fullB[k], 1); mbar_init(&emptyB[k], nw); }
+    for (int k = 0; k < kTileStagesA; ++k) mbar_init(&barA[k], 1);
+    for (int k = 0; k < kTileStagesB; ++k) mbar_init(&barB[k], 1);
     s_abort = 0;
     fence_mbar_init();
     fence_async_shared();
   }
   __syncthreads();
 
-  // accumulators: per-row reductions of the product phase; Gram blocks (per warp or per CTA)
+  // accumulators: per-row reductions of the product phase, one 2 x 2 block per Gram
   Acc2<kTileRowReds> acc;
 #pragma unroll
   for (int q = 0; q < kTileRowReds; ++q) acc.v[q][0] = acc.v[q][1] = make_float2(0.f, 0.f);
-  float2 w0[WBLK * 4], w1[WBLK * 4];  // warp Grams
-#pragma unroll
-  for (int e = 0; e < WBLK * 4; ++e) w0[e] = w1[e] = make_float2(0.f, 0.f);
-  float2 g0[4], g1[4];  // CTA Grams (s = 32)
+  float2 g0[4], g1[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) g0[e] = g1[e] = make_float2(0.f, 0.f);
-  const int gb = tid % NB, grow = tid / NB, RG = T / NB;  // CTA Grams: block and row group
+  const int gb = tid % NB, grow = tid / NB, RG = T / NB;  // Gram block and row group
   const int ga0 = 2 * (gb / GP), gc0 = 2 * (gb % GP);
 
-  // producer state (thread 0): phases armed per full barrier, for the bounded drain on abort
+  // producer state (thread 0): phases armed per barrier, for the bounded drain on abort
   int armA0 = 0, armA1 = 0, armA2 = 0, armB0 = 0, armB1 = 0;
   auto arm_a = [&](int k) { if (k == 0) ++armA0; else if (k == 1) ++armA1; else ++armA2; };
   auto rows_of = [&](int t) { const int64_t r0 = (int64_t)t * R; return (int)(n - r0 < R ? n - r0 : R); };
@@ -274,108 +241,78 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
     for (int k = 0; k < kTileStagesA; ++k) {
       const int t = t0 + k * tstep;
       if (t < ntiles) {
-        K::issue_a(a, L, baseA + k * strideA, &fullA[k], (int64_t)t * R, rows_of(t));
+        K::issue_a(a, L, baseA + k * strideA, &barA[k], (int64_t)t * R, rows_of(t));
         arm_a(k);
       }
     }
-    if (!mbar_wait(&fullA[0], 0)) {
-      s_abort = 1;
-    } else {
-      K::issue_b(a, L, baseB, reinterpret_cast<const int64_t*>(baseA + L.off_rp), &fullB[0], rows_of(t0));
-      ++armB0;
+    if constexpr (!STEN) {
+      if (!mbar_wait(&barA[0], 0)) {
+        s_abort = 1;
+      } else {
+        K::issue_b(a, L, baseB, reinterpret_cast<const int64_t*>(baseA + L.off_rp), &barB[0], rows_of(t0));
+        ++armB0;
+      }
     }
   }
 
-  int sa = 0, sb = 0, i = 0;
-  for (int t = t0; t < ntiles; t += tstep, ++i) {
+  // stage indices and the parity each barrier's pending phase completes with
+  int sa = 0, sb = 0;
+  uint32_t parA = 0, parB = 0;  // bit k: parity of barrier k's next phase to consume
+  for (int t = t0; t < ntiles; t += tstep) {
     unsigned char* A = baseA + sa * strideA;
     unsigned char* Bst = baseB + sb * strideB;
-    const uint32_t pa = (uint32_t)((i / kTileStagesA) & 1), pb = (uint32_t)((i >> 1) & 1);
     const int64_t r0 = (int64_t)t * R;
     const int rows = rows_of(t);
     const int sa1 = sa == kTileStagesA - 1 ? 0 : sa + 1;
-    // the producer: entries of the next tile into the B-stage the previous tile used, once every
-    // warp has handed it back (and the next tile's row pointers have arrived)
-    if (tid == 0 && t + tstep < ntiles && !s_abort) {
-      bool ok = true;
-      if (WG && i > 0) ok = mbar_wait_or_abort(&emptyB[1 - sb], (uint32_t)(((i - 1) >> 1) & 1), &s_abort);
-      ok = ok && mbar_wait_or_abort(&fullA[sa1], (uint32_t)(((i + 1) / kTileStagesA) & 1), &s_abort);
-      if (!ok) {
+    // the producer: entries of the next tile (its row pointers were issued a tile earlier)
+    if (!STEN && tid == 0 && t + tstep < ntiles && !s_abort) {
+      if (!mbar_wait(&barA[sa1], (parA >> sa1) & 1u)) {
         s_abort = 1;
       } else {
         fence_async_shared();
         K::issue_b(a, L, baseB + (1 - sb) * strideB,
-                   reinterpret_cast<const int64_t*>(baseA + sa1 * strideA + L.off_rp), &fullB[1 - sb],
+                   reinterpret_cast<const int64_t*>(baseA + sa1 * strideA + L.off_rp), &barB[1 - sb],
                    rows_of(t + tstep));
         if (sb == 0) ++armB1; else ++armB0;
       }
     }
-    bool ok = mbar_wait_or_abort(&fullA[sa], pa, &s_abort);
-    ok = ok && mbar_wait_or_abort(&fullB[sb], pb, &s_abort);
+    bool ok = mbar_wait(&barA[sa], (parA >> sa) & 1u);
+    if (!STEN) ok = ok && mbar_wait(&barB[sb], (parB >> sb) & 1u);
     if (!ok) s_abort = 1;
-    if constexpr (WG) {
-      // no CTA barrier inside this loop: a warp leaves as a whole (vote), never lane by lane
-      if (__any_sync(0xffffffffu, !ok || s_abort)) break;
-    }
-    const int64_t* rp = reinterpret_cast<const int64_t*>(A + L.off_rp);
-    const int32_t* col = reinterpret_cast<const int32_t*>(Bst + L.off_col);
-    const int64_t kb = rp[0] & ~(int64_t)3;
     // ---- product phase: row jj, column pair p
     Pair y = pzero();
     if (ok && jj < rows) {
       const int64_t j = r0 + jj;
       const int64_t e = j * S + 2 * p;
-      const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
-      auto gather = [&](int32_t c) {
-        const float4 v = Vq[(uint64_t)(uint32_t)c * (uint32_t)GP];
-        Pair q;
-        q.a = make_float2(v.x, v.y);
-        q.b = make_float2(v.z, v.w);
-        return q;
-      };
-      const int k0 = (int)(rp[jj] - kb), k1 = (int)(rp[jj + 1] - kb);
-      if (SPLIT) {
-        const float* val = reinterpret_cast<const float*>(Bst + L.off_val);
-        const float2 dgv = reinterpret_cast<const float2*>(A + L.off_dg)[jj];
-        const Pair xv = ld_pair(a.V, e);
-        y.a = cmul<float>(dgv, xv.a);
-        y.b = cmul<float>(dgv, xv.b);
-        int k = k0;
-        for (; k + 4 <= k1; k += 4) {
-          Pair x[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) x[u] = gather(col[k + u]);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            y.a = cfmareal<float>(val[k + u], x[u].a, y.a);
-            y.b = cfmareal<float>(val[k + u], x[u].b, y.b);
-          }
-        }
-        const int rem = k1 - k;
-        if (rem > 0) {
-          Pair x[3];
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            if (u < rem) x[u] = gather(col[k + u]);
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            if (u < rem) {
-              y.a = cfmareal<float>(val[k + u], x[u].a, y.a);
-              y.b = cfmareal<float>(val[k + u], x[u].b, y.b);
-            }
-        }
+      if constexpr (STEN) {
+        y = spmm2_row<true, false>(a, stc, stm, stp, j, p, e);
       } else {
-        const float2* val = reinterpret_cast<const float2*>(Bst + L.off_val);
+        const int64_t* rp = reinterpret_cast<const int64_t*>(A + L.off_rp);
+        const int32_t* col = reinterpret_cast<const int32_t*>(Bst + L.off_col);
+        const int64_t kb = rp[0] & ~(int64_t)3;
+        const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
+        auto gather = [&](int32_t c) {
+          const float4 v = Vq[(uint64_t)(uint32_t)c * (uint32_t)GP];
+          Pair q;
+          q.a = make_float2(v.x, v.y);
+          q.b = make_float2(v.z, v.w);
+          return q;
+        };
+        const int k0 = (int)(rp[jj] - kb), k1 = (int)(rp[jj + 1] - kb);
+        if (SPLIT) {
+          const float2 dgv = reinterpret_cast<const float2*>(A + L.off_dg)[jj];
+          const Pair xv = ld_pair(a.V, e);
+          y.a = cmul<float>(dgv, xv.a);
+          y.b = cmul<float>(dgv, xv.b);
+        }
+        // batches of four entries, the last 1-3 as one predicated batch: all loads of a batch in
+        // flight together (a longer single batch needs more registers than 2 CTAs per SM allow)
         int k = k0;
         for (; k + 4 <= k1; k += 4) {
           Pair x[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) x[u] = gather(col[k + u]);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            y.a = cfma<float>(val[k + u], x[u].a, y.a);
-            y.b = cfma<float>(val[k + u], x[u].b, y.b);
-          }
+          tile_fma<SPLIT, 4>(Bst + L.off_val, k, 4, x, y);
         }
         const int rem = k1 - k;
         if (rem > 0) {
@@ -383,12 +320,7 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
 #pragma unroll
           for (int u = 0; u < 3; ++u)
             if (u < rem) x[u] = gather(col[k + u]);
-#pragma unroll
-          for (int u = 0; u < 3; ++u)
-            if (u < rem) {
-              y.a = cfma<float>(val[k + u], x[u].a, y.a);
-              y.b = cfma<float>(val[k + u], x[u].b, y.b);
-            }
+          tile_fma<SPLIT, 3>(Bst + L.off_val, k, rem, x, y);
         }
       }
       if (a.ys != nullptr || a.ay != 1.0) {
@@ -426,78 +358,44 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
         }
       }
     }
-    if (NG > 0) st_pair(Yt, (int64_t)jj * S + 2 * p, y);  // rows past the tile's end hold zeros
-    if constexpr (WG) {
-      // ---- Grams of this warp's rows, then hand both stages back to the producer
-      __syncwarp();
-      if (NG > 0) {
-        const int r_lo = warp * RPW, r_hi = min(rows, r_lo + RPW);
-        const float2* U0 =
-            L.gram_u[0] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[0] * L.sz_u) : Yt;
-        if (r_hi > r_lo) warp_gram<S, WBLK>(U0, Yt, r_lo, r_hi, lane, w0);
-        if (NG > 1) {
-          const float2* U1 =
-              L.gram_u[1] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[1] * L.sz_u) : Yt;
-          if (r_hi > r_lo) warp_gram<S, WBLK>(U1, Yt, r_lo, r_hi, lane, w1);
-        }
-        __syncwarp();
+    if (NG > 0) st_pair(Yt, (int64_t)jj * S + 2 * p, y);
+    __syncthreads();
+    // ---- Gram phase: G[a][c] += conj(U[j][a]) Y[j][c] over the tile's rows, 2 x 2 blocks
+    if (NG > 0 && !s_abort && grow < RG) {
+      const float2* U0 = L.gram_u[0] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[0] * L.sz_u) : Yt;
+      gram_rows<S>(U0, Yt, ga0, gc0, grow, RG, rows, g0[0], g0[1], g0[2], g0[3]);
+      if (NG > 1) {
+        const float2* U1 =
+            L.gram_u[1] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[1] * L.sz_u) : Yt;
+        gram_rows<S>(U1, Yt, ga0, gc0, grow, RG, rows, g1[0], g1[1], g1[2], g1[3]);
       }
-      if (lane == 0) {
-        mbar_arrive(&emptyA[sa]);
-        mbar_arrive(&emptyB[sb]);
-      }
-      // the producer: row pointers, diagonal and U of the tile three ahead into this A-stage once
-      // every warp has handed it back (an abort is seen by every warp at its next vote)
-      if (tid == 0 && !s_abort) {
-        const int t3 = t + kTileStagesA * tstep;
-        if (t3 < ntiles) {
-          if (!mbar_wait_or_abort(&emptyA[sa], pa, &s_abort)) {
-            s_abort = 1;
-          } else {
-            fence_async_shared();
-            K::issue_a(a, L, A, &fullA[sa], (int64_t)t3 * R, rows_of(t3));
-            arm_a(sa);
-          }
-        }
-      }
-    } else {
-      // ---- CTA Grams (s = 32): every row of the tile, after a barrier
-      __syncthreads();
-      if (NG > 0 && !s_abort && grow < RG) {
-        const float2* U0 =
-            L.gram_u[0] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[0] * L.sz_u) : Yt;
-        gram_rows<S>(U0, Yt, ga0, gc0, grow, RG, rows, g0[0], g0[1], g0[2], g0[3]);
-        if (NG > 1) {
-          const float2* U1 =
-              L.gram_u[1] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[1] * L.sz_u) : Yt;
-          gram_rows<S>(U1, Yt, ga0, gc0, grow, RG, rows, g1[0], g1[1], g1[2], g1[3]);
-        }
-      }
-      __syncthreads();
-      if (s_abort) break;
-      if (tid == 0) {
-        const int t3 = t + kTileStagesA * tstep;
-        if (t3 < ntiles) {
-          fence_async_shared();
-          K::issue_a(a, L, A, &fullA[sa], (int64_t)t3 * R, rows_of(t3));
-          arm_a(sa);
-        }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    parA ^= 1u << sa;
+    parB ^= 1u << sb;
+    // the producer: row pointers, diagonal and U of the tile three ahead into the freed A-stage
+    if (tid == 0) {
+      const int t3 = t + kTileStagesA * tstep;
+      if (t3 < ntiles) {
+        fence_async_shared();
+        K::issue_a(a, L, A, &barA[sa], (int64_t)t3 * R, rows_of(t3));
+        arm_a(sa);
       }
     }
     sa = sa1;
     sb ^= 1;
   }
-  __syncthreads();  // every thread has left the loop (normally or after an abort)
 
   if (s_abort) {
-    // stop: wait (bounded) for the last phase armed on each full barrier, mark the partial record
+    // stop: wait (bounded) for the last phase armed on each barrier, mark the partial record
     if (tid == 0) {
       atomicAdd(&g_kr_wait_timeouts, 1u);
-      if (armA0 > 0) mbar_wait(&fullA[0], (uint32_t)((armA0 - 1) & 1));
-      if (armA1 > 0) mbar_wait(&fullA[1], (uint32_t)((armA1 - 1) & 1));
-      if (armA2 > 0) mbar_wait(&fullA[2], (uint32_t)((armA2 - 1) & 1));
-      if (armB0 > 0) mbar_wait(&fullB[0], (uint32_t)((armB0 - 1) & 1));
-      if (armB1 > 0) mbar_wait(&fullB[1], (uint32_t)((armB1 - 1) & 1));
+      if (armA0 > 0) mbar_wait(&barA[0], (uint32_t)((armA0 - 1) & 1));
+      if (armA1 > 0) mbar_wait(&barA[1], (uint32_t)((armA1 - 1) & 1));
+      if (armA2 > 0) mbar_wait(&barA[2], (uint32_t)((armA2 - 1) & 1));
+      if (armB0 > 0) mbar_wait(&barB[0], (uint32_t)((armB0 - 1) & 1));
+      if (armB1 > 0) mbar_wait(&barB[1], (uint32_t)((armB1 - 1) & 1));
     }
     if (rs.nred > 0) {
       float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
@@ -509,7 +407,8 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
 
   // ---- CTA reduction into the partial record (fixed order), reusing the staging buffers
   float2* red = reinterpret_cast<float2*>(tsm);  // [warp][compact per-row slots]
-  float2* gred = red + nw * L.ncompact;          // [gram][records][s x s]
+  const int nw = T >> 5;
+  float2* gred = red + nw * L.ncompact;          // [gram][row group][s x s]
 #pragma unroll
   for (int ri = 0; ri < kMaxRed; ++ri) {
     if (ri < rs.nred && rs.r[ri].kind != RED_GRAM) {
@@ -532,16 +431,9 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
       }
     }
   }
-  // Gram records: per (warp, row group) for warp Grams, per row group of the CTA for s = 32
-  const int nrec = WG ? nw * RGW : RG;
-  if constexpr (WG) {
-    if (NG > 0) warp_gram_stage<S, WBLK>(gred + (size_t)warp * RGW * S * S, lane, w0);
-    if (NG > 1) warp_gram_stage<S, WBLK>(gred + ((size_t)nrec + (size_t)warp * RGW) * S * S, lane, w1);
-  } else {
-    if (NG > 0 && grow < RG) {
-      gram_stage_block<S>(gred + (size_t)grow * S * S, ga0, gc0, g0[0], g0[1], g0[2], g0[3]);
-      if (NG > 1) gram_stage_block<S>(gred + ((size_t)RG + grow) * S * S, ga0, gc0, g1[0], g1[1], g1[2], g1[3]);
-    }
+  if (NG > 0 && grow < RG) {
+    gram_stage_block<S>(gred + (size_t)grow * S * S, ga0, gc0, g0[0], g0[1], g0[2], g0[3]);
+    if (NG > 1) gram_stage_block<S>(gred + ((size_t)RG + grow) * S * S, ga0, gc0, g1[0], g1[1], g1[2], g1[3]);
   }
   __syncthreads();
   float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
@@ -555,10 +447,10 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
       out[r.slot + q] = sum;
     }
   }
-  for (int gi = 0; gi < NG; ++gi) {  // Grams: sum over the records in order
+  for (int gi = 0; gi < NG; ++gi) {  // Grams: sum over row groups in order
     for (int q = tid; q < S * S; q += T) {
       float2 sum = make_float2(0.f, 0.f);
-      for (int g = 0; g < nrec; ++g) sum = cadd<float>(sum, gred[((size_t)gi * nrec + g) * S * S + q]);
+      for (int g = 0; g < RG; ++g) sum = cadd<float>(sum, gred[((size_t)gi * RG + g) * S * S + q]);
       out[L.gram_slot[gi] + q] = sum;
     }
   }

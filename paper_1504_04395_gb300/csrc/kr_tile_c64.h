@@ -16,6 +16,7 @@ constexpr int kTileRowReds = 2;        // per-row reductions (trace, column dots
 // computed on the host.
 struct TileLayout {
   int R;          // rows per tile (GP * R threads)
+  int mode;       // 0: CSR, 1: CSR with real off-diagonal entries and complex diagonal, 2: stencil
   int nu;         // distinct block operands U staged per tile (0..2)
   int ngram;      // fused Grams (0..2)
   int ystage;     // Y kept in shared memory for the Grams

@@ -11,7 +11,7 @@ namespace kr {
 
 constexpr int kTileMaxDynSmem = 200 * 1024;
 
-template <int GP, bool SPLIT, int NG>
+template <int GP, int MODE, int NG>
 static int tile_go(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout& L, const int* done,
                    cudaStream_t st) {
   static std::atomic<uint64_t> attr{0};
@@ -19,7 +19,7 @@ static int tile_go(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout&
   KR_CUDA(cudaGetDevice(&dev));
   const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t{1} << dev) : 0;
   if (bit == 0 || !(attr.load(std::memory_order_acquire) & bit)) {
-    KR_CUDA(cudaFuncSetAttribute(spmm_tile_kernel<GP, SPLIT, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    KR_CUDA(cudaFuncSetAttribute(spmm_tile_kernel<GP, MODE, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kTileMaxDynSmem));
     if (bit != 0) attr.fetch_or(bit, std::memory_order_acq_rel);
   }
@@ -33,34 +33,41 @@ static int tile_go(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout&
   if (it != occ_cache.end()) {
     occ = it->second;
   } else {
-    KR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_tile_kernel<GP, SPLIT, NG>, T, L.total));
+    KR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spmm_tile_kernel<GP, MODE, NG>, T, L.total));
     occ = std::max(1, std::min(occ, kCtasPerSm));
     occ_cache.emplace(key, occ);
   }
   const int64_t ntiles = (a.n + L.R - 1) / L.R;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sm_count() * occ);
-  spmm_tile_kernel<GP, SPLIT, NG><<<grid, T, L.total, st>>>(a, rs, L, done);
+  spmm_tile_kernel<GP, MODE, NG><<<grid, T, L.total, st>>>(a, rs, L, done);
   KR_CUDA(cudaGetLastError());
   return grid;
 }
 
-template <int GP, bool SPLIT>
+template <int GP, int MODE>
 static int tile_ng(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout& L, const int* done,
                    cudaStream_t st) {
-  if (L.ngram == 0) return tile_go<GP, SPLIT, 0>(a, rs, L, done, st);
-  if (L.ngram == 1) return tile_go<GP, SPLIT, 1>(a, rs, L, done, st);
-  return tile_go<GP, SPLIT, 2>(a, rs, L, done, st);
+  if (L.ngram == 0) return tile_go<GP, MODE, 0>(a, rs, L, done, st);
+  if (L.ngram == 1) return tile_go<GP, MODE, 1>(a, rs, L, done, st);
+  return tile_go<GP, MODE, 2>(a, rs, L, done, st);
+}
+
+template <int GP>
+static int tile_mode(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout& L, const int* done,
+                     cudaStream_t st) {
+  if (L.mode == TILE_STENCIL) return tile_ng<GP, TILE_STENCIL>(a, rs, L, done, st);
+  if (L.mode == TILE_SPLIT) return tile_ng<GP, TILE_SPLIT>(a, rs, L, done, st);
+  return tile_ng<GP, TILE_CSR>(a, rs, L, done, st);
 }
 
 int launch_spmm_tile(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout& L, int grid, const int* done,
                      cudaStream_t st) {
   (void)grid;
-  const bool split = a.split != 0;
   switch (a.s) {
-    case 4: return split ? tile_ng<2, true>(a, rs, L, done, st) : tile_ng<2, false>(a, rs, L, done, st);
-    case 8: return split ? tile_ng<4, true>(a, rs, L, done, st) : tile_ng<4, false>(a, rs, L, done, st);
-    case 16: return split ? tile_ng<8, true>(a, rs, L, done, st) : tile_ng<8, false>(a, rs, L, done, st);
-    case 32: return split ? tile_ng<16, true>(a, rs, L, done, st) : tile_ng<16, false>(a, rs, L, done, st);
+    case 4: return tile_mode<2>(a, rs, L, done, st);
+    case 8: return tile_mode<4>(a, rs, L, done, st);
+    case 16: return tile_mode<8>(a, rs, L, done, st);
+    case 32: return tile_mode<16>(a, rs, L, done, st);
   }
   throw CudaError{cudaErrorInvalidValue, "tile product: s out of range"};
 }

@@ -250,5 +250,32 @@ def test_c64_tile_product_full_size(kr, s, kind, adj):
     op.close()
 
 
+@pytest.mark.parametrize("s", [4, 8, 16, 32])
+@pytest.mark.parametrize("kind", ["gram", "trace"])
+def test_c64_tile_stencil_reductions(kr, s, kind):
+    """The tile kernel on the matrix-free stencil (no staged matrix): the product bitwise equal to
+    the CSR storage's, the fused Gram / trace against FP64 on the host from the complex64 inputs."""
+    cd = ConvDiff((37, 21, 19), (0.4, -0.3, 0.2), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    centre, minus, plus = cd.coefficients()
+    st = kr.Operator.stencil(cd.dims, centre, minus, plus)
+    csr = kr.Operator(cd.n, rp, ci, v)
+    V = c64(gaussian_block(cd.n, s, seed=s))
+    U = c64(gaussian_block(cd.n, s, seed=s + 1))
+    Ys, outs = kr.kr_op_apply_reduce_c64(st, dev32(V), dev32(U), kind=kind)
+    Yc, outc = kr.kr_op_apply_reduce_c64(csr, dev32(V), dev32(U), kind=kind)
+    assert torch.equal(Ys, Yc)
+    Yk = host(Ys)
+    if kind == "gram":
+        want, bound = U.conj().T @ Yk, np.abs(U).T @ np.abs(Yk)
+    else:
+        want, bound = np.array([np.sum(U.conj() * Yk)]), np.array([np.sum(np.abs(U) * np.abs(Yk))])
+    for out in (outs, outc):
+        got = host(out).reshape(want.shape)
+        assert np.all(np.abs(got - want) <= 1e-4 * bound)
+    st.close()
+    csr.close()
+
+
 def test_no_device_wait_ran_out(kr):
     assert kr.kr_take_device_timeouts(reset=False) == 0

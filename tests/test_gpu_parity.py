@@ -452,8 +452,8 @@ def test_fused_schedule_against_oracle_and_literal(kr, method):
     s = 4
     Bv = 16.0 * n * s
     saved = (literal_b - fused_b) / Bv
-    # eGl-BiCG: three blocks fewer, one n-vector (1/s of a block) more; Gl-BiCG: two blocks fewer
-    assert saved == pytest.approx(3.0 - 1.0 / s if method == "egl_bicg" else 2.0, abs=0.02), saved
+    # eGl-BiCG: three blocks fewer, two n-vectors (1/s of a block each) more; Gl-BiCG: two blocks fewer
+    assert saved == pytest.approx(3.0 - 2.0 / s if method == "egl_bicg" else 2.0, abs=0.02), saved
     op.close()
 
 
