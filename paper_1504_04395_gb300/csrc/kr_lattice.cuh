@@ -77,12 +77,7 @@ __global__ void __launch_bounds__(kThreads) lattice_kernel(SpmmArgs<T> a, RedSet
     for (int k = 0; k < 4; ++k) y[k] = czero<T>();
     if (act) {
       int64_t xc[4];
-      int64_t rem = x;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        xc[q] = rem % a.ldims[q];
-        rem /= a.ldims[q];
-      }
+      grid_coords<4>(x, 4, a.ldiv32, a.ldims, a.ldiv, xc);
 #pragma unroll
       for (int k = 0; k < 4; ++k) y[k] = cmul<T>(dg, Vc[(x * 12 + k * 3 + ci) * s]);
       // hops one after another (a rolled loop): unrolled, the compiler precomputes the
@@ -213,12 +208,7 @@ __global__ void __launch_bounds__(kThreads) lattice_site_kernel(SpmmArgs<T> a, R
     for (int k = 0; k < 12; ++k) y[k] = czero<T>();
     if (act) {
       int64_t xc[4];
-      int64_t rem = x;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        xc[q] = rem % a.ldims[q];
-        rem /= a.ldims[q];
-      }
+      grid_coords<4>(x, 4, a.ldiv32, a.ldims, a.ldiv, xc);
 #pragma unroll
       for (int k = 0; k < 12; ++k) y[k] = cmul<T>(dg, Vc[(x * 12 + k) * s]);
 #pragma unroll 1

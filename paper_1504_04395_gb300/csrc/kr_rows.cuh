@@ -49,6 +49,34 @@ struct LatHop {
   double2 rc[4];
 };
 
+// Division of a 32-bit unsigned index by an invariant divisor d >= 1 with one high multiply
+// (Granlund and Montgomery, "Division by invariant integers using multiplication", PLDI 1994,
+// Sec. 4): with l = ceil(log2 d) and mag = floor(2^32 (2^l - d) / d) + 1,
+// floor(x / d) = (t + ((x - t) >> min(l, 1))) >> max(l - 1, 0), t = floor(x mag / 2^32),
+// exact for every 0 <= x < 2^32.  Grid coordinates of the matrix-free operators use it in place
+// of a 64-bit division, which costs tens of instructions per row.
+struct FastDivU32 {
+  uint32_t d, mag;
+  int sh1, sh2;
+};
+inline FastDivU32 make_fastdiv(uint32_t d) {
+  int l = 0;
+  while (l < 32 && (uint64_t(1) << l) < d) ++l;
+  FastDivU32 f;
+  f.d = d;
+  // (2^l - d) < d <= 2^32, so the 64-bit product cannot overflow
+  f.mag = (uint32_t)((((uint64_t(1) << l) - d) << 32) / d + 1);
+  f.sh1 = l < 1 ? l : 1;
+  f.sh2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fastdiv(uint32_t x, const FastDivU32& f) {
+  const uint32_t t = __umulhi(x, f.mag);
+  return (t + ((x - t) >> f.sh1)) >> f.sh2;
+}
+#endif
+
 // ---------------------------------------------------------------------------------------
 // SpMM: Y = ay * (A V) + bz * Z  (ay, bz real; optionally ay scaled by a device scalar)
 // ---------------------------------------------------------------------------------------
@@ -74,8 +102,10 @@ struct SpmmArgs {
   // y_j = c V_j + sum_a m_a V_{j - st_a} [x_a > 0] + p_a V_{j + st_a} [x_a < N_a - 1]
   int nst;
   int sreal;                 // all neighbour coefficients real
+  int sdiv32;                // n < 2^32: coordinates through sdiv (else 64-bit division)
   int64_t sdims[3];
   int64_t sstr[3];
+  FastDivU32 sdiv[3];        // divisors sdims[q]
   double2 sc;                // centre
   double2 sm[3], sp[3];      // minus / plus neighbour along each axis
   // matrix-free 4D lattice operator (lat = 1 replaces the CSR; rows (site * 4 + spin) * 3 + colour):
@@ -84,10 +114,48 @@ struct SpmmArgs {
   int lat;
   int64_t ldims[4];          // sites per axis (axis 0 fastest), periodic
   int64_t lstr[4];           // site strides
+  int ldiv32;                // sites < 2^32: coordinates through ldiv
+  FastDivU32 ldiv[4];        // divisors ldims[q]
   const C2<T>* links;        // [4][sites][3][3] (row-major 3 x 3), scaled by the hop coefficient
   double2 ldiag;
   LatHop lh[8];              // hop 2 mu: forward (+mu), hop 2 mu + 1: backward (-mu)
 };
+
+#ifdef __CUDACC__
+// Coordinates (axis 0 fastest) of index j < prod(dims[0..nd)) of a grid with nd <= ND axes; the
+// last axis takes the quotient left over and needs no division.  use32: j and every extent fit in
+// 32 bits, so the divisions go through the precomputed FastDivU32.
+template <int ND>
+__device__ __forceinline__ void grid_coords(int64_t j, int nd, int use32, const int64_t* dims,
+                                            const FastDivU32* div, int64_t (&xc)[ND]) {
+  if (use32) {
+    uint32_t rem = (uint32_t)j;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      xc[q] = 0;
+      if (q + 1 < nd) {
+        const uint32_t qt = fastdiv(rem, div[q]);
+        xc[q] = (int64_t)(rem - qt * div[q].d);
+        rem = qt;
+      } else if (q + 1 == nd) {
+        xc[q] = (int64_t)rem;
+      }
+    }
+  } else {
+    int64_t rem = j;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      xc[q] = 0;
+      if (q + 1 < nd) {
+        xc[q] = rem % dims[q];
+        rem /= dims[q];
+      } else if (q + 1 == nd) {
+        xc[q] = rem;
+      }
+    }
+  }
+}
+#endif
 
 // ---------------------------------------------------------------------------------------
 // Linear combinations: out_o = sum_t  src_t * coef_t

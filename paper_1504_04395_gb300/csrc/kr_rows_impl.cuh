@@ -175,11 +175,7 @@ __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoe
     // centre, then -axis d-1 .. -axis 0, then +axis 0 .. +axis d-1
     const C2<T> stc = sk.c;
     int64_t xc[3];
-    int64_t rem = j;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
-    }
+    grid_coords<3>(j, a.nst, a.sdiv32, a.sdims, a.sdiv, xc);
     if (act) {
       y = cmul<T>(stc, a.V[j * s + c]);
 #pragma unroll

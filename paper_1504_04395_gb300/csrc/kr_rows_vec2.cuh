@@ -168,10 +168,7 @@ __device__ __forceinline__ Pair spmm2_row(const SpmmArgs<float>& a, const float2
   Pair y = pzero();
   if constexpr (STENCIL) {
     int64_t xc[3];
-    int64_t rem = j;
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      if (q < a.nst) { xc[q] = rem % a.sdims[q]; rem /= a.sdims[q]; }
+    grid_coords<3>(j, a.nst, a.sdiv32, a.sdims, a.sdiv, xc);
     const Pair xv = ld_pair(a.V, e);
     y.a = cmul<float>(stc, xv.a);
     y.b = cmul<float>(stc, xv.b);

@@ -69,10 +69,14 @@ SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s) {
   if (op.lat.on) {
     const LatticeSpec& L = op.lat;
     a.lat = 1;
+    int64_t sites = 1;
     for (int q = 0; q < 4; ++q) {
       a.ldims[q] = L.dims[q];
       a.lstr[q] = L.str[q];
+      sites *= L.dims[q];
     }
+    a.ldiv32 = sites <= (int64_t)UINT32_MAX;
+    for (int q = 0; q < 4; ++q) a.ldiv[q] = make_fastdiv(a.ldiv32 ? (uint32_t)L.dims[q] : 1u);
     if constexpr (sizeof(T) == 8) a.links = reinterpret_cast<const C2<T>*>(L.links);
     else a.links = reinterpret_cast<const C2<T>*>(L.links32);
     a.ldiag = adjoint ? L.diagH : L.diag;
@@ -90,6 +94,8 @@ SpmmArgs<T> op_spmm_args(const Operator& op, bool adjoint, int s) {
       a.sm[q] = st.m[q];
       a.sp[q] = st.p[q];
     }
+    a.sdiv32 = op.n <= (int64_t)UINT32_MAX;
+    for (int q = 0; q < 3; ++q) a.sdiv[q] = make_fastdiv(a.sdiv32 ? (uint32_t)st.dims[q] : 1u);
     a.sc = st.c;
     a.split = 1;  // profile accounting: real neighbours
     a.nnz = op.nnz - op.n;
