@@ -213,9 +213,9 @@ static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& 
   const bool sten = a.nst > 0;
   const int s = a.s;
   if (s != 4 && s != 8 && s != 16 && s != 32) return false;
-  if (sten && a.nst > 3) return false;
   const int GP = s / 2;
-  const int R = kTileThreads / GP;
+  const int R = std::min(128, kTileThreadsMax / GP);
+  if (!sten && (int64_t)R * a.maxrow > kTileEcap) return false;
   if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
   if (rs.nred > kMaxRed) return false;
   L = TileLayout{};
@@ -255,31 +255,20 @@ static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& 
   L.ncompact = nc;
   const bool split = !sten && a.split != 0;
   L.mode = sten ? 2 : (split ? 1 : 0);
-  // entries staged per tile: [rowptr[r0] & ~3, rowptr[r0 + R]) holds at most R * maxrow + 3
-  const int64_t ecap = sten ? 0 : (((int64_t)R * a.maxrow + 3 + 3) & ~(int64_t)3);
-  if (ecap > (int64_t)1 << 16) return false;
-  L.ecap = (int)ecap;
-  const int slot = s * 8;  // one gathered row of V
+  L.off_rp = 0;
   L.sz_rp = sten ? 0 : round16i((int64_t)(R + 2) * 8);
-  L.off_dg = 0;
+  L.off_dg = L.sz_rp;
   L.sz_dg = split ? R * 8 : 0;
-  L.off_u = L.sz_dg;
-  L.sz_u = R * slot;
+  L.off_u = L.sz_rp + L.sz_dg;
+  L.sz_u = R * s * 8;
   L.off_col = 0;
-  L.sz_col = sten ? 0 : round16i((ecap + 8) * 4);
+  L.sz_col = sten ? 0 : round16i((int64_t)(kTileEcap + 8) * 4);
   L.off_val = L.sz_col;
-  L.sz_val = sten ? 0 : round16i((ecap + 8) * (split ? 4 : 8));
-  L.off_ge = split ? R * slot : 0;
-  L.stride_a1 = L.sz_rp;
-  L.stride_a2 = L.sz_dg + L.nu * L.sz_u;
-  L.stride_b = L.sz_col + L.sz_val;
-  L.stride_g = sten ? kTileStencilSlots * R * slot : (int)(L.off_ge + ecap * slot);
-  L.off_a2 = kTileStagesA1 * L.stride_a1;
-  L.off_b = L.off_a2 + kTileStagesA2 * L.stride_a2;
-  L.off_g = L.off_b + kTileStagesB * L.stride_b;
-  L.off_y = L.off_g + kTileStagesG * L.stride_g;
-  const int staged = L.off_y + (L.ystage ? R * slot : 0);
-  const int T = kTileThreads;
+  L.sz_val = sten ? 0 : round16i((int64_t)(kTileEcap + 8) * (split ? 4 : 8));
+  const int strideA = L.sz_rp + L.sz_dg + L.nu * L.sz_u, strideB = L.sz_col + L.sz_val;
+  L.off_y = kTileStagesA * strideA + kTileStagesB * strideB;
+  const int staged = L.off_y + (L.ystage ? R * s * 8 : 0);
+  const int T = GP * R;
   const int final_red = (T / 32) * nc * 8 + ngram * (T / (GP * GP)) * s * s * 8;
   L.total = std::max(staged, final_red);
   return L.total <= kMaxDynSmem;

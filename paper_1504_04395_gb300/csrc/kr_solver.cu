@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <limits>
 
 #include "kr_engine.h"
 #include "kr_precond.h"
@@ -151,6 +152,26 @@ bool offdiag_real(int64_t n, const std::vector<int64_t>& rp, const std::vector<i
   return true;
 }
 
+// A stored value in the element type.  For complex64 copies the conversion follows IEEE round to
+// nearest, with the overflow case written out: magnitudes from 2^128 - 2^103 (half an ulp above
+// the largest float) up become infinities, those between the largest float and that bound round
+// to it, NaN stays NaN.  An operator beyond the complex64 range then gives non-finite inner
+// solves, which the defect correction detects (it finishes in FP64).
+template <typename T>
+static inline T narrow(double x) {
+  if constexpr (sizeof(T) == 8) {
+    return x;
+  } else {
+    constexpr float inf = std::numeric_limits<float>::infinity();
+    constexpr float fmax = std::numeric_limits<float>::max();
+    const double ax = std::fabs(x);
+    if (std::isnan(x)) return std::numeric_limits<float>::quiet_NaN();
+    if (ax >= 0x1.ffffffp+127) return x < 0 ? -inf : inf;
+    if (ax > (double)fmax) return x < 0 ? -fmax : fmax;
+    return (float)x;
+  }
+}
+
 template <typename T>
 void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
             const std::vector<double>& v, bool split) {
@@ -160,7 +181,7 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
   d.split = split ? 1 : 0;
   if (!split) {
     std::vector<C2<T>> hv(d.nnz);
-    for (int64_t k = 0; k < d.nnz; ++k) hv[k] = mk<T>((T)v[2 * k], (T)v[2 * k + 1]);
+    for (int64_t k = 0; k < d.nnz; ++k) hv[k] = mk<T>(narrow<T>(v[2 * k]), narrow<T>(v[2 * k + 1]));
     KR_CUDA(cudaMalloc(&d.rowptr, sizeof(int64_t) * (n + 1) + kCsrPad));
     KR_CUDA(cudaMalloc(&d.colidx, sizeof(int32_t) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
     KR_CUDA(cudaMalloc(&d.vals, sizeof(C2<T>) * std::max<int64_t>(d.nnz, 1) + kCsrPad));
@@ -181,9 +202,9 @@ void upload(CsrDev<T>& d, int64_t n, const std::vector<int64_t>& rp, const std::
     double dr = 0.0, di = 0.0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
       if (ci[k] == i) { dr += v[2 * k]; di += v[2 * k + 1]; }
-      else { oci.push_back(ci[k]); ov.push_back((T)v[2 * k]); }
+      else { oci.push_back(ci[k]); ov.push_back(narrow<T>(v[2 * k])); }
     }
-    dg[i] = mk<T>((T)dr, (T)di);
+    dg[i] = mk<T>(narrow<T>(dr), narrow<T>(di));
     orp[i + 1] = (int64_t)oci.size();
   }
   d.nnz = orp[n];
@@ -223,7 +244,7 @@ void build_operator_device(Operator& op, bool want32) {
     }
     if (want32 && !L.links32) {
       std::vector<float2> h32(cnt);
-      for (size_t i = 0; i < cnt; ++i) h32[i] = make_float2((float)L.h_links[2 * i], (float)L.h_links[2 * i + 1]);
+      for (size_t i = 0; i < cnt; ++i) h32[i] = make_float2(narrow<float>(L.h_links[2 * i]), narrow<float>(L.h_links[2 * i + 1]));
       KR_CUDA(cudaMalloc(&L.links32, sizeof(float2) * cnt));
       KR_CUDA(cudaMemcpy(L.links32, h32.data(), sizeof(float2) * cnt, cudaMemcpyHostToDevice));
     }

@@ -1,39 +1,35 @@
-// Complex64 CSR product with fused reductions: row tiles staged by TMA bulk copies, gathers of V
-// staged by asynchronous copies.
+// Complex64 CSR product with fused reductions, row tiles staged by TMA bulk copies.
 //
 // The product Y = A V of the complex64 inner solves reads the matrix once for all s columns
 // (Sec. 1 of the paper).  The per-thread kernels (kr_rows_vec2.cuh) chain three dependent
 // global loads per row -- row pointers, the row's indices and values, then the gathered rows
 // of V -- and stay latency-bound near half of HBM; with a fused s x s Gram their s
-// accumulators per thread cost occupancy as well.  Here each CTA of 256 threads walks row tiles
-// of R = 256 / (s/2) rows through three pipelines:
+// accumulators per thread cost occupancy as well.  Here each CTA walks row tiles of R rows:
 //
-//   * A (three tiles ahead): one thread issues 1D bulk copies (cp.async.bulk, completion on an
-//     mbarrier) of the tile's row pointers, complex diagonal and the reductions' U blocks, and a
-//     bulk L2 prefetch of the tile's own rows of V;
-//   * B (two tiles ahead): the same thread copies the tile's column indices and values, whose
-//     range it reads from the row pointers already in shared memory;
-//   * G (one tile ahead): every thread copies the rows of V its own (row, column pair) will
-//     multiply -- one 16-byte cp.async per stored entry (CSR) or per stencil neighbour -- into
-//     shared memory, and waits for them one tile later.  No gathered value occupies a register
-//     while it is in flight, and the gathers of the next tile overlap the product, the stores
-//     and the Gram of the current one;
-//   * the product of a (row, pair) then reads its rows from shared memory, the fused s x s
-//     Grams U^H Y are formed after each tile from shared-memory copies of Y and U (every thread
-//     owning a 2 x 2 block of entries for a subset of the tile's rows), and per-row reductions
-//     (trace, column dots, norm, economic sums) accumulate as in the column-pair kernel.
+//   * one thread issues 1D bulk copies (cp.async.bulk, completion on an mbarrier) of the
+//     tile's row pointers, complex diagonal and the reductions' U blocks three tiles ahead (and
+//     a bulk L2 prefetch of the tile's rows of V),
+//     and of the tile's column indices and values one tile ahead (their range is read from
+//     the row pointers already in shared memory), so only the gathers of V remain
+//     synchronous loads;
+//   * GP = s/2 threads per row, each owning a column pair (16-byte gathers and stores); a
+//     row's entries come from shared memory and all its gathers are in flight together;
+//   * fused s x s Grams U^H Y are formed after each tile from shared-memory copies of Y and U,
+//     every thread owning a 2 x 2 block of entries for a subset of the tile's rows, so the
+//     Gram costs neither registers in the product nor occupancy;
+//   * per-row reductions (trace, column dots, norm, economic sums) accumulate as in the
+//     column-pair kernel.
 //
 // Every output entry is computed with the operations and in the order of the other product
-// kernels (diagonal first, then the stored entries in order; for the stencil the centre, the
-// minus neighbours, then the plus neighbours), so Y is bitwise the same; the partial sums of the
-// reductions are grouped differently and agree to FP32 rounding.  The CTA partial records have the
-// layout of the other kernels (same slots), reduced by reduce_slots_kernel in a fixed order.
+// kernels (diagonal first, then the stored entries in order), so Y is bitwise the same; the
+// partial sums of the reductions are grouped differently and agree to FP32 rounding.  The CTA
+// partial records have the layout of the other kernels (same slots), reduced by
+// reduce_slots_kernel in a fixed order.
 //
 // Every mbarrier wait is bounded.  A wait that runs out (which correct copies never do) makes
-// the CTA stop computing: all of its threads leave together after the next barrier, after waiting
-// (again bounded) for the bulk copies issued and for their own asynchronous copies, with NaN in the
-// CTA's partial record and the device counter g_kr_wait_timeouts incremented
-// (kr_take_device_timeouts reads it).
+// the CTA stop computing: all of its threads leave together at the next barrier, after waiting
+// (again bounded) for the copies they issued, with NaN in the CTA's partial record and the
+// device counter g_kr_wait_timeouts incremented (kr_take_device_timeouts reads it).
 #pragma once
 
 #include "kr_rows_vec2.cuh"
@@ -90,17 +86,6 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ uint32_t round16(uint64_t b) { return (uint32_t)((b + 15) & ~(uint64_t)15); }
 
-// 16-byte asynchronous copy global -> shared (cache at L2 only), tracked per thread by groups
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// all of this thread's groups but the newest N have landed in shared memory
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // operator storage of a tile launch
 enum TileMode : int { TILE_CSR = 0, TILE_SPLIT = 1, TILE_STENCIL = 2 };
 
@@ -111,23 +96,18 @@ struct TileKernel {
   static constexpr bool SPLIT = MODE == TILE_SPLIT;
   static constexpr bool STEN = MODE == TILE_STENCIL;
 
-  // A1-stage copy of a tile (CSR): its row pointers
-  static __device__ void issue_a1(const SpmmArgs<float>& a, unsigned char* sm, uint64_t* bar, int64_t r0, int rows) {
-    const uint32_t brp = round16((uint64_t)(rows + 1) * 8);
-    mbar_arrive_expect(bar, brp);
-    bulk_load(sm, a.rowptr + r0, brp, bar);
-  }
-
-  // A2-stage copies of a tile: complex diagonal (split storage) and the U operands (none when the
-  // launch has neither: the barrier is then never armed), and a bulk L2 prefetch of the tile's rows
-  // of V, which its diagonal and its neighbouring rows gather
-  static __device__ void issue_a2(const SpmmArgs<float>& a, const TileLayout& L, unsigned char* sm, uint64_t* bar,
-                                  int64_t r0, int rows) {
+  // A-stage copies of a tile into stage `sm`: row pointers and diagonal (CSR), U operands; and a
+  // bulk L2 prefetch of the tile's rows of V
+  static __device__ void issue_a(const SpmmArgs<float>& a, const TileLayout& L, unsigned char* sm, uint64_t* bar,
+                                 int64_t r0, int rows) {
+    const uint32_t brp = STEN ? 0 : round16((uint64_t)(rows + 1) * 8);
     const uint32_t bdg = SPLIT ? round16((uint64_t)rows * 8) : 0;
     const uint32_t bu = (uint32_t)rows * S * 8;  // a multiple of 16 (S even)
+    mbar_arrive_expect(bar, brp + bdg + bu * L.nu);
+    // the tile's own rows of V into L2 (gathered by its diagonal and by the neighbouring tiles'
+    // rows, which other CTAs process at about the same time): one instruction, no completion
     prefetch_l2_bulk(reinterpret_cast<const float2*>(a.V) + r0 * S, bu);
-    if (!SPLIT && L.nu == 0) return;
-    mbar_arrive_expect(bar, bdg + bu * L.nu);
+    if (!STEN) bulk_load(sm + L.off_rp, a.rowptr + r0, brp, bar);
     if (SPLIT) bulk_load(sm + L.off_dg, a.diag + r0, bdg, bar);
     for (int u = 0; u < L.nu; ++u)
       bulk_load(sm + L.off_u + u * L.sz_u, reinterpret_cast<const float2*>(L.U[u]) + r0 * S, bu, bar);
@@ -144,49 +124,6 @@ struct TileKernel {
       bulk_load(sm_b + L.off_col, a.colidx + k0, bc, bar);
       if (SPLIT) bulk_load(sm_b + L.off_val, a.offr + k0, bv, bar);
       else bulk_load(sm_b + L.off_val, a.vals + k0, bv, bar);
-    }
-  }
-
-  // G-stage copies of one thread, row jj (global row j) and column pair p of a tile: the rows of V
-  // its product multiplies, each 16 bytes into its slot (slots of S complex entries).  CSR: the
-  // diagonal's row (split storage) into slot jj, stored entry k of the tile into slot k - kb of the
-  // entry region (rp: the tile's staged row pointers, Bst its staged entries).  Stencil: slot
-  // 7 jj + m, m = 0 centre, 1..3 minus neighbours along axes 2, 1, 0, 4..6 plus neighbours along
-  // axes 0, 1, 2; returns the bit mask of the neighbours present.
-  static __device__ uint32_t issue_g(const SpmmArgs<float>& a, const TileLayout& L, unsigned char* G,
-                                     const int64_t* rp, const unsigned char* Bst, int64_t j, int jj, int p) {
-    const float2* Vp = a.V + 2 * p;
-    if constexpr (STEN) {
-      float2* g = reinterpret_cast<float2*>(G) + (int64_t)jj * kTileStencilSlots * S + 2 * p;
-      int64_t xc[3];
-      grid_coords<3>(j, a.nst, a.sdiv32, a.sdims, a.sdiv, xc);
-      uint32_t mask = 1;
-      cp_async16(g, Vp + j * S);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int qa = 2 - q;
-        if (qa < a.nst && xc[qa] > 0) {
-          mask |= 1u << (1 + q);
-          cp_async16(g + (1 + q) * S, Vp + (j - a.sstr[qa]) * S);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q < a.nst && xc[q] < a.sdims[q] - 1) {
-          mask |= 1u << (4 + q);
-          cp_async16(g + (4 + q) * S, Vp + (j + a.sstr[q]) * S);
-        }
-      }
-      return mask;
-    } else {
-      const int32_t* col = reinterpret_cast<const int32_t*>(Bst + L.off_col);
-      const int64_t kb = rp[0] & ~(int64_t)3;
-      const int k0 = (int)(rp[jj] - kb), k1 = (int)(rp[jj + 1] - kb);
-      if (SPLIT) cp_async16(reinterpret_cast<float2*>(G) + (int64_t)jj * S + 2 * p, Vp + j * S);
-      float2* ge = reinterpret_cast<float2*>(G + L.off_ge) + 2 * p;
-      for (int k = k0; k < k1; ++k)
-        cp_async16(ge + (int64_t)k * S, Vp + (int64_t)(uint32_t)col[k] * S);
-      return 0;
     }
   }
 };
@@ -216,50 +153,41 @@ __device__ __forceinline__ void gram_stage_block(float2* G, int a0, int c0, floa
   G[(a0 + 1) * S + c0 + 1] = x11;
 }
 
-// Pipeline stages in tile order.  Per-stage mbarrier bookkeeping packed into bits: parity words
-// hold, per stage k, the parity of the next phase to consume (bit k); armed words hold bit 2k =
-// stage k armed at least once and bit 2k + 1 = parity of its number of arms.
-template <int N>
-__device__ __forceinline__ int next_stage(int k) { return k + 1 == N ? 0 : k + 1; }
-__device__ __forceinline__ void note_armed(uint32_t& m, int k) {
-  m |= 1u << (2 * k);
-  m ^= 1u << (2 * k + 1);
-}
-// bounded wait for the last phase armed on each of N barriers (the drain of an abort)
-template <int N>
-__device__ __forceinline__ void drain(uint64_t* bar, uint32_t m) {
+
+// y += sum over the batch's m entries of val[k + u] * x[u] (real values for the split storage)
+template <bool SPLIT, int NBATCH>
+__device__ __forceinline__ void tile_fma(const unsigned char* valbuf, int k, int m, const Pair (&x)[NBATCH], Pair& y) {
+  if constexpr (SPLIT) {
+    const float* val = reinterpret_cast<const float*>(valbuf);
 #pragma unroll
-  for (int k = 0; k < N; ++k)
-    if ((m >> (2 * k)) & 1u) mbar_wait(&bar[k], ((m >> (2 * k + 1)) & 1u) ^ 1u);
-}
-// consume the next phase of stage k: bounded wait, then flip the stage's parity bit
-__device__ __forceinline__ bool take_phase(uint64_t* bar, uint32_t& par, int k) {
-  const bool ok = mbar_wait(&bar[k], (par >> k) & 1u);
-  par ^= 1u << k;
-  return ok;
+    for (int u = 0; u < NBATCH; ++u)
+      if (u < m) {
+        y.a = cfmareal<float>(val[k + u], x[u].a, y.a);
+        y.b = cfmareal<float>(val[k + u], x[u].b, y.b);
+      }
+  } else {
+    const float2* val = reinterpret_cast<const float2*>(valbuf);
+#pragma unroll
+    for (int u = 0; u < NBATCH; ++u)
+      if (u < m) {
+        y.a = cfma<float>(val[k + u], x[u].a, y.a);
+        y.b = cfma<float>(val[k + u], x[u].b, y.b);
+      }
+  }
 }
 
 // MODE: TileMode; NG: fused Grams (0..2); at most kTileRowReds per-row reductions.  The Grams are
 // formed by the whole CTA after each tile from the shared-memory copies of Y and U.
-//
-// Tile i of a CTA (its i-th tile, global index t0 + i * gridDim.x) moves through the stages
-// A1 (i % 6), B (i % 4), A2 (i % 3) and G (i % 2).  Iteration i: thread 0 copies A1 of tile i + 5
-// and, once A1 of tile i + 3 has landed, B of tile i + 3; every thread waits for A1 and B of tile
-// i + 1 and issues its gathers of tile i + 1, then waits for its gathers of tile i and for A2 of
-// tile i, forms its product and reductions; after the CTA's Gram of tile i, thread 0 copies A2 of
-// tile i + 3 into the stage tile i freed.  Each refilled stage was last read before the barriers
-// of the previous iteration.
 template <int GP, int MODE, int NG>
-__global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<float> a, RedSet rs, TileLayout L,
-                                                                     const int* done) {
+__global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<float> a, RedSet rs, TileLayout L,
+                                                                        const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   using K = TileKernel<GP, MODE>;
   constexpr int S = K::S;
   constexpr int NB = K::NB;
   constexpr bool SPLIT = K::SPLIT, STEN = K::STEN;
-  constexpr int NA1 = kTileStagesA1, NA2 = kTileStagesA2, NBS = kTileStagesB;
   extern __shared__ __align__(128) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t barA1[NA1], barA2[NA2], barB[NBS];
+  __shared__ __align__(8) uint64_t barA[kTileStagesA], barB[kTileStagesB];
   __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int T = blockDim.x;  // = GP * R
@@ -269,13 +197,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<flo
   const int lane = tid & 31, warp = tid >> 5;
   const int p = tid % GP;   // column pair of the product phase
   const int jj = tid / GP;  // row of the tile in the product phase
-  const bool hasA2 = SPLIT || L.nu > 0;
-  unsigned char* baseA1 = tsm;
-  unsigned char* baseA2 = tsm + L.off_a2;
-  unsigned char* baseB = tsm + L.off_b;
-  unsigned char* baseG = tsm + L.off_g;
+  const int strideA = L.sz_rp + L.sz_dg + L.nu * L.sz_u;
+  const int strideB = L.sz_col + L.sz_val;
+  unsigned char* baseA = tsm;
+  unsigned char* baseB = tsm + kTileStagesA * strideA;
   float2* Yt = reinterpret_cast<float2*>(tsm + L.off_y);
-  auto rp_of = [&](int k) { return reinterpret_cast<const int64_t*>(baseA1 + k * L.stride_a1); };
   // stencil coefficients, converted once (double -> float runs on the FP64 pipe)
   float2 stc = make_float2(0.f, 0.f), stm[3], stp[3];
   if constexpr (STEN) {
@@ -288,9 +214,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<flo
   }
 
   if (tid == 0) {
-    for (int k = 0; k < NA1; ++k) mbar_init(&barA1[k], 1);
-    for (int k = 0; k < NA2; ++k) mbar_init(&barA2[k], 1);
-    for (int k = 0; k < NBS; ++k) mbar_init(&barB[k], 1);
+    for (int k = 0; k < kTileStagesA; ++k) mbar_init(&barA[k], 1);
+    for (int k = 0; k < kTileStagesB; ++k) mbar_init(&barB[k], 1);
     s_abort = 0;
     fence_mbar_init();
     fence_async_shared();
@@ -307,158 +232,95 @@ __global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<flo
   const int gb = tid % NB, grow = tid / NB, RG = T / NB;  // Gram block and row group
   const int ga0 = 2 * (gb / GP), gc0 = 2 * (gb % GP);
 
+  // producer state (thread 0): phases armed per barrier, for the bounded drain on abort
+  int armA0 = 0, armA1 = 0, armA2 = 0, armB0 = 0, armB1 = 0;
+  auto arm_a = [&](int k) { if (k == 0) ++armA0; else if (k == 1) ++armA1; else ++armA2; };
   auto rows_of = [&](int t) { const int64_t r0 = (int64_t)t * R; return (int)(n - r0 < R ? n - r0 : R); };
   const int t0 = blockIdx.x, tstep = gridDim.x;
-  auto tile_of = [&](int i) { return t0 + i * tstep; };  // may pass ntiles: callers compare first
-  // producer (thread 0) state: phases armed per barrier, and its own parity of the A1 phases it
-  // waits for before issuing B (one tile ahead of the consumers' A1 waits)
-  uint32_t armA1 = 0, armA2 = 0, armB = 0, parP = 0;
   if (tid == 0) {
-    if constexpr (!STEN) {
-      for (int k = 0; k < NA1 - 1; ++k)
-        if (tile_of(k) < ntiles) {
-          K::issue_a1(a, baseA1 + k * L.stride_a1, &barA1[k], (int64_t)tile_of(k) * R, rows_of(tile_of(k)));
-          note_armed(armA1, k);
-        }
-    }
-    for (int k = 0; k < NA2; ++k)
-      if (tile_of(k) < ntiles) {
-        K::issue_a2(a, L, baseA2 + k * L.stride_a2, &barA2[k], (int64_t)tile_of(k) * R, rows_of(tile_of(k)));
-        if (hasA2) note_armed(armA2, k);
+    for (int k = 0; k < kTileStagesA; ++k) {
+      const int t = t0 + k * tstep;
+      if (t < ntiles) {
+        K::issue_a(a, L, baseA + k * strideA, &barA[k], (int64_t)t * R, rows_of(t));
+        arm_a(k);
       }
+    }
     if constexpr (!STEN) {
-      for (int k = 0; k < NBS - 1; ++k) {
-        if (tile_of(k) >= ntiles) break;
-        if (!take_phase(barA1, parP, k)) {
-          s_abort = 1;
-          break;
-        }
-        K::issue_b(a, L, baseB + k * L.stride_b, rp_of(k), &barB[k], rows_of(tile_of(k)));
-        note_armed(armB, k);
+      if (!mbar_wait(&barA[0], 0)) {
+        s_abort = 1;
+      } else {
+        K::issue_b(a, L, baseB, reinterpret_cast<const int64_t*>(baseA + L.off_rp), &barB[0], rows_of(t0));
+        ++armB0;
       }
     }
   }
-  __syncthreads();
 
-  int sa1 = 0, sa2 = 0, sb = 0, sg = 0;  // stages of the current tile
-  uint32_t parA1 = 0, parA2 = 0, parB = 0;
-  // the first tile's gathers: every thread waits for its A1- and B-stage, then issues its copies
-  bool okc = s_abort == 0;
-  uint32_t maskc = 0, maskn = 0;
-  if constexpr (!STEN) {
-    if (okc) {
-      const bool w1 = take_phase(barA1, parA1, 0);
-      const bool w2 = take_phase(barB, parB, 0);
-      okc = w1 && w2;
-    }
-  }
-  if (!okc) s_abort = 1;
-  if (okc && jj < rows_of(t0)) maskc = K::issue_g(a, L, baseG, rp_of(0), baseB, (int64_t)t0 * R + jj, jj, p);
-  cp_async_commit();
-
-  for (int i = 0; tile_of(i) < ntiles; ++i) {
-    const int t = tile_of(i);
+  // stage indices and the parity each barrier's pending phase completes with
+  int sa = 0, sb = 0;
+  uint32_t parA = 0, parB = 0;  // bit k: parity of barrier k's next phase to consume
+  for (int t = t0; t < ntiles; t += tstep) {
+    unsigned char* A = baseA + sa * strideA;
+    unsigned char* Bst = baseB + sb * strideB;
     const int64_t r0 = (int64_t)t * R;
     const int rows = rows_of(t);
-    const int64_t tn = (int64_t)t + tstep;
-    const int sa1n = next_stage<NA1>(sa1), sbn = next_stage<NBS>(sb);
-    // the producer: row pointers of tile i + 5, entries of tile i + 3
-    if (!STEN && tid == 0 && !s_abort) {
-      fence_async_shared();
-      const int64_t t5 = (int64_t)t + 5 * (int64_t)tstep, t3 = (int64_t)t + 3 * (int64_t)tstep;
-      if (t5 < ntiles) {
-        const int k5 = (sa1 + 5) % NA1;
-        K::issue_a1(a, baseA1 + k5 * L.stride_a1, &barA1[k5], t5 * R, rows_of((int)t5));
-        note_armed(armA1, k5);
-      }
-      if (t3 < ntiles) {
-        const int k3 = (sa1 + 3) % NA1, b3 = (sb + 3) % NBS;
-        if (!take_phase(barA1, parP, k3)) {
-          s_abort = 1;
-        } else {
-          K::issue_b(a, L, baseB + b3 * L.stride_b, rp_of(k3), &barB[b3], rows_of((int)t3));
-          note_armed(armB, b3);
-        }
+    const int sa1 = sa == kTileStagesA - 1 ? 0 : sa + 1;
+    // the producer: entries of the next tile (its row pointers were issued a tile earlier)
+    if (!STEN && tid == 0 && t + tstep < ntiles && !s_abort) {
+      if (!mbar_wait(&barA[sa1], (parA >> sa1) & 1u)) {
+        s_abort = 1;
+      } else {
+        fence_async_shared();
+        K::issue_b(a, L, baseB + (1 - sb) * strideB,
+                   reinterpret_cast<const int64_t*>(baseA + sa1 * strideA + L.off_rp), &barB[1 - sb],
+                   rows_of(t + tstep));
+        if (sb == 0) ++armB1; else ++armB0;
       }
     }
-    // this thread's gathers of the next tile, into the other G-stage
-    bool okn = false;
-    if (tn < ntiles) {
-      okn = true;
-      if constexpr (!STEN) {
-        const bool w1 = take_phase(barA1, parA1, sa1n);
-        const bool w2 = take_phase(barB, parB, sbn);
-        okn = w1 && w2;
-      }
-      if (!okn) s_abort = 1;
-      if (okn && jj < rows_of((int)tn))
-        maskn = K::issue_g(a, L, baseG + (sg ^ 1) * L.stride_g, rp_of(sa1n), baseB + sbn * L.stride_b,
-                           tn * R + jj, jj, p);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();  // this thread's gathers of tile i are in shared memory
-    bool okA2 = true;
-    if (hasA2) {
-      okA2 = take_phase(barA2, parA2, sa2);
-      if (!okA2) s_abort = 1;
-    }
-    const unsigned char* A2 = baseA2 + sa2 * L.stride_a2;
-    const unsigned char* Bst = baseB + sb * L.stride_b;
-    const unsigned char* G = baseG + sg * L.stride_g;
-    // ---- product phase: row jj, column pair p, from the gathered rows
+    bool ok = mbar_wait(&barA[sa], (parA >> sa) & 1u);
+    if (!STEN) ok = ok && mbar_wait(&barB[sb], (parB >> sb) & 1u);
+    if (!ok) s_abort = 1;
+    // ---- product phase: row jj, column pair p
     Pair y = pzero();
-    if (okc && okA2 && jj < rows) {
+    if (ok && jj < rows) {
       const int64_t j = r0 + jj;
       const int64_t e = j * S + 2 * p;
       if constexpr (STEN) {
-        const float2* g = reinterpret_cast<const float2*>(G) + (int64_t)jj * kTileStencilSlots * S + 2 * p;
-        const Pair xv = ld_pair(g, 0);
-        y.a = cmul<float>(stc, xv.a);
-        y.b = cmul<float>(stc, xv.b);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int qa = 2 - q;
-          if ((maskc >> (1 + q)) & 1u) {
-            const Pair x = ld_pair(g, (1 + q) * S);
-            if (a.sreal) { y.a = cfmareal<float>(stm[qa].x, x.a, y.a); y.b = cfmareal<float>(stm[qa].x, x.b, y.b); }
-            else { y.a = cfma<float>(stm[qa], x.a, y.a); y.b = cfma<float>(stm[qa], x.b, y.b); }
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if ((maskc >> (4 + q)) & 1u) {
-            const Pair x = ld_pair(g, (4 + q) * S);
-            if (a.sreal) { y.a = cfmareal<float>(stp[q].x, x.a, y.a); y.b = cfmareal<float>(stp[q].x, x.b, y.b); }
-            else { y.a = cfma<float>(stp[q], x.a, y.a); y.b = cfma<float>(stp[q], x.b, y.b); }
-          }
-        }
+        y = spmm2_row<true, false>(a, stc, stm, stp, j, p, e);
       } else {
-        const int64_t* rp = rp_of(sa1);
+        const int64_t* rp = reinterpret_cast<const int64_t*>(A + L.off_rp);
+        const int32_t* col = reinterpret_cast<const int32_t*>(Bst + L.off_col);
         const int64_t kb = rp[0] & ~(int64_t)3;
+        const float4* Vq = reinterpret_cast<const float4*>(a.V) + p;
+        auto gather = [&](int32_t c) {
+          const float4 v = Vq[(uint64_t)(uint32_t)c * (uint32_t)GP];
+          Pair q;
+          q.a = make_float2(v.x, v.y);
+          q.b = make_float2(v.z, v.w);
+          return q;
+        };
         const int k0 = (int)(rp[jj] - kb), k1 = (int)(rp[jj + 1] - kb);
         if (SPLIT) {
-          const float2 dgv = reinterpret_cast<const float2*>(A2 + L.off_dg)[jj];
-          const Pair xv = ld_pair(reinterpret_cast<const float2*>(G), (int64_t)jj * S + 2 * p);
+          const float2 dgv = reinterpret_cast<const float2*>(A + L.off_dg)[jj];
+          const Pair xv = ld_pair(a.V, e);
           y.a = cmul<float>(dgv, xv.a);
           y.b = cmul<float>(dgv, xv.b);
         }
-        const float2* ge = reinterpret_cast<const float2*>(G + L.off_ge) + 2 * p;
-        if constexpr (SPLIT) {
-          const float* val = reinterpret_cast<const float*>(Bst + L.off_val);
-          for (int k = k0; k < k1; ++k) {
-            const Pair x = ld_pair(ge, (int64_t)k * S);
-            const float v = val[k];
-            y.a = cfmareal<float>(v, x.a, y.a);
-            y.b = cfmareal<float>(v, x.b, y.b);
-          }
-        } else {
-          const float2* val = reinterpret_cast<const float2*>(Bst + L.off_val);
-          for (int k = k0; k < k1; ++k) {
-            const Pair x = ld_pair(ge, (int64_t)k * S);
-            const float2 v = val[k];
-            y.a = cfma<float>(v, x.a, y.a);
-            y.b = cfma<float>(v, x.b, y.b);
-          }
+        // batches of four entries, the last 1-3 as one predicated batch: all loads of a batch in
+        // flight together (a longer single batch needs more registers than 2 CTAs per SM allow)
+        int k = k0;
+        for (; k + 4 <= k1; k += 4) {
+          Pair x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) x[u] = gather(col[k + u]);
+          tile_fma<SPLIT, 4>(Bst + L.off_val, k, 4, x, y);
+        }
+        const int rem = k1 - k;
+        if (rem > 0) {
+          Pair x[3];
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+            if (u < rem) x[u] = gather(col[k + u]);
+          tile_fma<SPLIT, 3>(Bst + L.off_val, k, rem, x, y);
         }
       }
       if (a.ys != nullptr || a.ay != 1.0) {
@@ -485,7 +347,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<flo
           Pair u = pzero();
           if (r.kind == RED_TRACE || r.kind == RED_CDOT) {
             if (L.red_u[ri] >= 0)
-              u = ld_pair(reinterpret_cast<const float2*>(A2 + L.off_u + L.red_u[ri] * L.sz_u), (int64_t)jj * S + 2 * p);
+              u = ld_pair(reinterpret_cast<const float2*>(A + L.off_u + L.red_u[ri] * L.sz_u), (int64_t)jj * S + 2 * p);
             else
               u = y;  // the product itself (U == nullptr, or U is this launch's Y)
           } else if (r.kind == RED_SUMV || r.kind == RED_GRAMV) {
@@ -498,47 +360,42 @@ __global__ void __launch_bounds__(kTileThreads, 2) spmm_tile_kernel(SpmmArgs<flo
     }
     if (NG > 0) st_pair(Yt, (int64_t)jj * S + 2 * p, y);
     __syncthreads();
-    // s_abort is written only before the barrier above (by a wait that ran out) and read by every
-    // thread between the two barriers, so all threads take the same decision
-    const bool stop = s_abort != 0;
     // ---- Gram phase: G[a][c] += conj(U[j][a]) Y[j][c] over the tile's rows, 2 x 2 blocks
-    if (NG > 0 && !stop && grow < RG) {
-      const float2* U0 = L.gram_u[0] >= 0 ? reinterpret_cast<const float2*>(A2 + L.off_u + L.gram_u[0] * L.sz_u) : Yt;
+    if (NG > 0 && !s_abort && grow < RG) {
+      const float2* U0 = L.gram_u[0] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[0] * L.sz_u) : Yt;
       gram_rows<S>(U0, Yt, ga0, gc0, grow, RG, rows, g0[0], g0[1], g0[2], g0[3]);
       if (NG > 1) {
         const float2* U1 =
-            L.gram_u[1] >= 0 ? reinterpret_cast<const float2*>(A2 + L.off_u + L.gram_u[1] * L.sz_u) : Yt;
+            L.gram_u[1] >= 0 ? reinterpret_cast<const float2*>(A + L.off_u + L.gram_u[1] * L.sz_u) : Yt;
         gram_rows<S>(U1, Yt, ga0, gc0, grow, RG, rows, g1[0], g1[1], g1[2], g1[3]);
       }
     }
     __syncthreads();
-    if (stop) break;
-    // the producer: diagonal and U of the tile three ahead into the A2-stage this tile freed
+    if (s_abort) break;
+    parA ^= 1u << sa;
+    parB ^= 1u << sb;
+    // the producer: row pointers, diagonal and U of the tile three ahead into the freed A-stage
     if (tid == 0) {
-      const int64_t t3 = (int64_t)t + 3 * (int64_t)tstep;
+      const int t3 = t + kTileStagesA * tstep;
       if (t3 < ntiles) {
         fence_async_shared();
-        K::issue_a2(a, L, baseA2 + sa2 * L.stride_a2, &barA2[sa2], t3 * R, rows_of((int)t3));
-        if (hasA2) note_armed(armA2, sa2);
+        K::issue_a(a, L, A, &barA[sa], (int64_t)t3 * R, rows_of(t3));
+        arm_a(sa);
       }
     }
-    sa1 = sa1n;
-    sb = sbn;
-    sa2 = next_stage<NA2>(sa2);
-    sg ^= 1;
-    okc = okn;
-    maskc = maskn;
+    sa = sa1;
+    sb ^= 1;
   }
 
   if (s_abort) {
-    // stop: this thread's copies land, the producer waits (bounded) for the last phase armed on
-    // each barrier, the partial record is marked
-    cp_async_wait<0>();
+    // stop: wait (bounded) for the last phase armed on each barrier, mark the partial record
     if (tid == 0) {
       atomicAdd(&g_kr_wait_timeouts, 1u);
-      drain<NA1>(barA1, armA1);
-      drain<NA2>(barA2, armA2);
-      drain<NBS>(barB, armB);
+      if (armA0 > 0) mbar_wait(&barA[0], (uint32_t)((armA0 - 1) & 1));
+      if (armA1 > 0) mbar_wait(&barA[1], (uint32_t)((armA1 - 1) & 1));
+      if (armA2 > 0) mbar_wait(&barA[2], (uint32_t)((armA2 - 1) & 1));
+      if (armB0 > 0) mbar_wait(&barB[0], (uint32_t)((armB0 - 1) & 1));
+      if (armB1 > 0) mbar_wait(&barB[1], (uint32_t)((armB1 - 1) & 1));
     }
     if (rs.nred > 0) {
       float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;

@@ -193,10 +193,10 @@ def test_mixed_solve_with_and_without_pairs(kr, method):
 @pytest.mark.parametrize("method", ["bl_bicg_rq", "bl_bicgstab"])
 def test_mixed_block_methods(kr, method):
     """Block methods under the defect correction.  With its s x s Gram products accumulated in
-    FP32, the complex64 inner Bl-BiCG-rQ solve on this problem stops reducing the residual (an
-    oracle Bl-BiCG run with only its Grams rounded to FP32 diverges the same way); the defect
-    correction then restores X and finishes with the FP64 solver.  Either way the result meets
-    the FP64 tolerance."""
+    FP32, the complex64 inner Bl-BiCG-rQ solve on this problem can stop reducing the residual,
+    depending on how the partial sums are grouped (an oracle Bl-BiCG run with only its Grams
+    rounded to FP32 diverges); the defect correction then restores X and finishes with the FP64
+    solver.  Either way the result meets the FP64 tolerance."""
     cd = ConvDiff((24, 24, 24), (0.6, 0.6, 0.6), 0.05j)
     rp, ci, v = convdiff_csr(cd)
     op = kr.Operator(cd.n, rp, ci, v)
@@ -206,11 +206,32 @@ def test_mixed_block_methods(kr, method):
     X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=3000,
                           precision=kr.FP32_REFINE)
     assert info.status == "OK", info
-    if method == "bl_bicg_rq":
-        assert info.fp64_iters > 0, info
     assert info.iters < 3000
     X = host(X)
     assert np.linalg.norm(B - A @ X) / np.linalg.norm(B) <= 1.01e-10
+    assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
+    op.close()
+
+
+@pytest.mark.parametrize("method", ["egl_bicg", "bl_bicg_rq"])
+def test_mixed_fallback_to_fp64(kr, method):
+    """The defect correction's FP64 finish: with every entry of A scaled by 2^130 (exact in FP64,
+    beyond the complex64 range) the complex64 inner solve returns no finite correction, so the
+    first defect-correction step does not reduce the residual; X is restored and the FP64 solver
+    finishes to the requested tolerance.  The solution is 2^-130 times that of the unscaled system."""
+    cd = ConvDiff((16, 16, 16), (0.6, 0.6, 0.6), 0.05j)
+    rp, ci, v = convdiff_csr(cd)
+    scale = 2.0 ** 130
+    op = kr.Operator(cd.n, rp, ci, v * scale)
+    B = gaussian_block(cd.n, 4, seed=9)
+    A = oracle.csr_matrix_from_arrays(cd.n, rp, ci, v)
+    X_lu = splu(A.tocsc()).solve(B) / scale
+    X, info = kr.kr_solve(op, method, torch.from_numpy(B).cuda(), tol=1e-10, maxit=3000,
+                          precision=kr.FP32_REFINE)
+    assert info.status == "OK", info
+    assert info.fp64_iters > 0 and info.outer_iters == 2, info
+    X = host(X)
+    assert np.linalg.norm(B - scale * (A @ X)) / np.linalg.norm(B) <= 1.01e-10
     assert np.linalg.norm(X - X_lu) / np.linalg.norm(X_lu) < 1e-8
     op.close()
 
