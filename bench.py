@@ -481,8 +481,8 @@ def gpu_arm(args):
     roofline = {
         "kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
         "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
-        "peak_source": "measured: FP64 FMA probe kr_probe_fma (8 independent DFMA chains per thread, 4x256 "
-                       "threads per SM, best of 3 launches, CUDA events), this run",
+        "peak_source": "measured: FP64 FMA probe kr_probe_fma (16 independent DFMA chains per thread, 4x256 "
+                       "threads per SM, best of 5 launches after 3 warm-up launches, CUDA events), this run",
         "nominal_fp64_tflops": FP64_NOMINAL_TFLOPS, "measured_fp32_tflops": peaks["fp32"],
         "timing": "per-launch CUDA events in a separate profiled step after the timed region",
         "launches": pd["launches"], "avg_launch_ms": pd["ms"] / max(pd["launches"], 1),
