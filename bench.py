@@ -903,7 +903,8 @@ def spmm_rates(args):
     tiles staged by bulk copies, column pairs, one column per thread) and complex128.  CUDA events
     over 30 launches after 5 warm-up launches, inputs larger than L2.  Algorithmic bytes: the CSR
     arrays once (real off-diagonal storage: 4-byte index and one real value per off-diagonal entry,
-    complex diagonal, row pointers), V and U read, Y written."""
+    complex diagonal, row pointers), V and U read, Y written.  The same operator as a matrix-free
+    7-point stencil (no matrix bytes): complex64 on the plane-marching kernel and on column pairs."""
     import torch
     import paper_1504_04395_gb300 as kr
     from paper_1504_04395_gb300 import build
@@ -959,7 +960,8 @@ def spmm_rates(args):
     Y = torch.empty_like(V)
     byts = 3 * 8 * n * s
     for kind in ("gram", "trace"):
-        for vname, (tile, pairs) in (("tile", (True, True)), ("pairs", (False, True))):
+        # "plane": the plane-marching kernel (TMA tensor copies of halo'd x-y tiles, 2D/3D grids)
+        for vname, (tile, pairs) in (("plane", (True, True)), ("pairs", (False, True))):
             if kind == "gram" and s > 16 and not tile:
                 continue
             kr.kr_set_tile_kernels(tile)

@@ -9,6 +9,7 @@
 #include "kr_rows_impl.cuh"
 #include "kr_rows_vec2.cuh"
 #include "kr_lattice.cuh"
+#include "kr_plane_c64.h"
 #include "kr_tile_c64.h"
 
 namespace kr {
@@ -206,20 +207,13 @@ static void lin2_dispatch(const LinArgs& a, const RedSet& rs, int& grid, const i
 // ---------------------------------------------------------------------------------------
 inline int round16i(int64_t b) { return (int)((b + 15) & ~(int64_t)15); }
 
-// Shared-memory layout and reduction maps of a tile launch; false when the launch does not fit
-// the tile kernel (then the other kernels run it).
-static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L) {
-  if (a.lat) return false;
-  const bool sten = a.nst > 0;
+// Reduction maps of a staged product launch (row tiles or planes): the distinct block operands U,
+// the Grams' operands and slots, the per-row reductions' accumulators; false when the launch has
+// more than kTileMaxU distinct operands, two Grams, kTileRowReds per-row reductions, or a U that
+// is not 16-byte aligned.
+static bool red_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L) {
   const int s = a.s;
-  if (s != 4 && s != 8 && s != 16 && s != 32) return false;
-  const int GP = s / 2;
-  const int R = std::min(128, kTileThreadsMax / GP);
-  if (!sten && (int64_t)R * a.maxrow > kTileEcap) return false;
-  if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
-  if (rs.nred > kMaxRed) return false;
   L = TileLayout{};
-  L.R = R;
   int ngram = 0, nc = 0, nrow = 0;
   for (int ri = 0; ri < kMaxRed; ++ri) L.red_u[ri] = -1;
   for (int ri = 0; ri < rs.nred; ++ri) {
@@ -253,6 +247,24 @@ static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& 
   L.ngram = ngram;
   L.ystage = ngram > 0 ? 1 : 0;
   L.ncompact = nc;
+  return true;
+}
+
+// Shared-memory layout and reduction maps of a tile launch; false when the launch does not fit
+// the tile kernel (then the other kernels run it).
+static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L) {
+  if (a.lat) return false;
+  const bool sten = a.nst > 0;
+  const int s = a.s;
+  if (s != 4 && s != 8 && s != 16 && s != 32) return false;
+  const int GP = s / 2;
+  const int R = std::min(128, kTileThreadsMax / GP);
+  if (!sten && (int64_t)R * a.maxrow > kTileEcap) return false;
+  if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
+  if (rs.nred > kMaxRed) return false;
+  if (!red_layout(a, rs, L)) return false;
+  L.R = R;
+  const int ngram = L.ngram, nc = L.ncompact;
   const bool split = !sten && a.split != 0;
   L.mode = sten ? 2 : (split ? 1 : 0);
   L.off_rp = 0;
@@ -274,6 +286,51 @@ static bool tile_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& 
   return L.total <= kMaxDynSmem;
 }
 
+// Geometry, shared-memory layout and reduction maps of a plane launch (kr_plane_c64.cuh); false when
+// the launch does not qualify (then the row-tile or per-row kernels run it).  The x-y tile is the
+// largest of the candidates whose stages fit two CTAs per SM (else one).
+static bool plane_layout(const SpmmArgs<float>& a, const RedSet& rs, TileLayout& L, PlaneGeom& P) {
+  if (a.lat || a.nst < 2 || a.nst > 3) return false;
+  const int s = a.s;
+  if (s != 2 && s != 4 && s != 8 && s != 16 && s != 32) return false;
+  if (!aligned16(a.V) || !aligned16(a.Y) || !aligned16(a.Z)) return false;
+  if (rs.nred > kMaxRed) return false;
+  const int64_t nx = a.sdims[0], ny = a.sdims[1], nz = a.nst == 3 ? a.sdims[2] : 1;
+  if (a.sstr[0] != 1 || a.sstr[1] != nx || (a.nst == 3 && a.sstr[2] != nx * ny)) return false;
+  if (nx * ny * nz != a.n || a.n > 0x7fffffffLL) return false;
+  if (!red_layout(a, rs, L) || L.nu > 1) return false;
+  const int GP = s / 2;
+  const int T = kPlaneThreads;
+  auto r128 = [](int64_t b) { return (int)((b + 127) & ~(int64_t)127); };
+  static const int cand[][2] = {{32, 8}, {32, 4}, {32, 2}, {16, 4}, {16, 2}, {32, 1}, {16, 1}, {8, 1}};
+  const int final_red = (T / 32) * L.ncompact * 8 + L.ngram * (T / (GP * GP)) * s * s * 8;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int cap = (pass == 0 ? 110 * 1024 : kMaxDynSmem) - 128;  // the launch adds 128 bytes of alignment
+    for (const auto& c : cand) {
+      const int tx = (int)std::min<int64_t>(c[0], nx), ty = (int)std::min<int64_t>(c[1], ny);
+      PlaneGeom g{};
+      g.nx = (int)nx; g.ny = (int)ny; g.nz = (int)nz;
+      g.tx = tx; g.ty = ty;
+      g.ntx = (int)((nx + tx - 1) / tx);
+      g.nty = (int)((ny + ty - 1) / ty);
+      g.ipt = (tx * ty * GP + T - 1) / T;
+      if (g.ipt > kPlaneMaxIpt) continue;
+      g.off_v = 0;
+      g.stride_v = r128((int64_t)(tx + 2) * (ty + 2) * s * 8);
+      g.off_u = kPlaneStagesV * g.stride_v;
+      g.stride_u = L.nu > 0 ? r128((int64_t)tx * ty * s * 8) : 0;
+      g.off_y = g.off_u + kPlaneStagesU * g.stride_u;
+      const int staged = g.off_y + (L.ngram > 0 ? r128((int64_t)tx * ty * s * 8) : 0);
+      g.total = std::max(staged, final_red);
+      if (g.total <= cap) {
+        P = g;
+        return true;
+      }
+    }
+  }
+  return false;
+}
+
 template <typename T>
 int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* done, cudaStream_t st) {
   ProfToken tk = prof_begin(sizeof(T) == 4 ? KC_SPMM32 : KC_SPMM, st);
@@ -284,6 +341,11 @@ int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* don
   }
   if constexpr (sizeof(T) == 4) {
     TileLayout L;
+    PlaneGeom P;
+    if (!done_launch && tile_kernels_enabled() && plane_layout(a, rs, L, P)) {
+      grid = launch_spmm_plane(a, rs, L, P, done, st);
+      done_launch = true;
+    }
     if (!done_launch && tile_kernels_enabled() && tile_layout(a, rs, L)) {
       grid = launch_spmm_tile(a, rs, L, grid, done, st);
       done_launch = true;

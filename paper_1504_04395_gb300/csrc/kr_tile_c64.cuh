@@ -84,6 +84,27 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Rings of mbarrier stages: bookkeeping packed into bits.  Parity words hold, per stage k, the
+// parity of the next phase to consume (bit k); armed words hold bit 2k = stage k armed at least
+// once and bit 2k + 1 = parity of its number of arms.
+__device__ __forceinline__ void note_armed(uint32_t& m, int k) {
+  m |= 1u << (2 * k);
+  m ^= 1u << (2 * k + 1);
+}
+// bounded wait for the last phase armed on each of N barriers (the drain of an abort)
+template <int N>
+__device__ __forceinline__ void drain_stages(uint64_t* bar, uint32_t m) {
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if ((m >> (2 * k)) & 1u) mbar_wait(&bar[k], ((m >> (2 * k + 1)) & 1u) ^ 1u);
+}
+// consume the next phase of stage k: bounded wait, then flip the stage's parity bit
+__device__ __forceinline__ bool take_phase(uint64_t* bar, uint32_t& par, int k) {
+  const bool ok = mbar_wait(&bar[k], (par >> k) & 1u);
+  par ^= 1u << k;
+  return ok;
+}
+
 __device__ __forceinline__ uint32_t round16(uint64_t b) { return (uint32_t)((b + 15) & ~(uint64_t)15); }
 
 // operator storage of a tile launch
@@ -154,6 +175,73 @@ __device__ __forceinline__ void gram_stage_block(float2* G, int a0, int c0, floa
 }
 
 
+// Fixed-order CTA reduction of the fused reductions into the CTA's partial record (slots as in
+// the other row kernels), reusing shared memory from `sm`: per-row reductions summed over warps
+// in order, Grams over row groups in order.  acc: per-thread sums of the per-row reductions (column
+// pair tid % GP); g0, g1: this thread's 2 x 2 block (ga0, gc0) of each Gram over row group grow.
+template <int GP, int NG>
+__device__ __forceinline__ void cta_partials(unsigned char* sm, const RedSet& rs, const TileLayout& L,
+                                             const Acc2<kTileRowReds>& acc, const float2 (&g0)[4],
+                                             const float2 (&g1)[4], int grow, int RG, int ga0, int gc0) {
+  constexpr int S = 2 * GP;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  float2* red = reinterpret_cast<float2*>(sm);  // [warp][compact per-row slots]
+  const int nw = T >> 5;
+  float2* gred = red + nw * L.ncompact;         // [gram][row group][s x s]
+#pragma unroll
+  for (int ri = 0; ri < kMaxRed; ++ri) {
+    if (ri < rs.nred && rs.r[ri].kind != RED_GRAM) {
+      const RedSpec& r = rs.r[ri];
+      const int k = L.red_k[ri];
+      float2* dst = red + warp * L.ncompact + L.red_c[ri];
+      float2 v0 = acc.v[0][0], v1 = acc.v[0][1];
+      if (k == 1) { v0 = acc.v[1][0]; v1 = acc.v[1][1]; }
+      if (r.kind == RED_CDOT || r.kind == RED_GRAMV) {
+#pragma unroll
+        for (int off = 16; off >= GP; off >>= 1) {
+          v0 = cadd<float>(v0, shfl_down<float>(v0, off));
+          v1 = cadd<float>(v1, shfl_down<float>(v1, off));
+        }
+        if (lane < GP) { dst[2 * lane] = v0; dst[2 * lane + 1] = v1; }
+      } else {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v0 = cadd<float>(v0, shfl_down<float>(v0, off));
+        if (lane == 0) dst[0] = v0;
+      }
+    }
+  }
+  if (NG > 0 && grow < RG) {
+    gram_stage_block<S>(gred + (size_t)grow * S * S, ga0, gc0, g0[0], g0[1], g0[2], g0[3]);
+    if (NG > 1) gram_stage_block<S>(gred + ((size_t)RG + grow) * S * S, ga0, gc0, g1[0], g1[1], g1[2], g1[3]);
+  }
+  __syncthreads();
+  float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
+  for (int ri = 0; ri < rs.nred; ++ri) {  // per-row reductions: sum over warps in order
+    const RedSpec& r = rs.r[ri];
+    if (r.kind == RED_GRAM) continue;
+    const int cnt = (r.kind == RED_CDOT || r.kind == RED_GRAMV) ? S : 1;
+    for (int q = tid; q < cnt; q += T) {
+      float2 sum = make_float2(0.f, 0.f);
+      for (int w = 0; w < nw; ++w) sum = cadd<float>(sum, red[w * L.ncompact + L.red_c[ri] + q]);
+      out[r.slot + q] = sum;
+    }
+  }
+  for (int gi = 0; gi < NG; ++gi) {  // Grams: sum over row groups in order
+    for (int q = tid; q < S * S; q += T) {
+      float2 sum = make_float2(0.f, 0.f);
+      for (int g = 0; g < RG; ++g) sum = cadd<float>(sum, gred[((size_t)gi * RG + g) * S * S + q]);
+      out[L.gram_slot[gi] + q] = sum;
+    }
+  }
+}
+
+// A CTA that stopped on a wait that ran out marks its partial record with NaN
+__device__ __forceinline__ void cta_partials_nan(const RedSet& rs) {
+  if (rs.nred == 0) return;
+  float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
+  for (int q = threadIdx.x; q < rs.nslots; q += blockDim.x) out[q] = make_float2(__int_as_float(0x7fc00000), 0.f);
+}
+
 // y += sum over the batch's m entries of val[k + u] * x[u] (real values for the split storage)
 template <bool SPLIT, int NBATCH>
 __device__ __forceinline__ void tile_fma(const unsigned char* valbuf, int k, int m, const Pair (&x)[NBATCH], Pair& y) {
@@ -194,7 +282,6 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
   const int R = L.R;
   const int64_t n = a.n;
   const int ntiles = (int)((n + R - 1) / R);
-  const int lane = tid & 31, warp = tid >> 5;
   const int p = tid % GP;   // column pair of the product phase
   const int jj = tid / GP;  // row of the tile in the product phase
   const int strideA = L.sz_rp + L.sz_dg + L.nu * L.sz_u;
@@ -397,63 +484,11 @@ __global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<
       if (armB0 > 0) mbar_wait(&barB[0], (uint32_t)((armB0 - 1) & 1));
       if (armB1 > 0) mbar_wait(&barB[1], (uint32_t)((armB1 - 1) & 1));
     }
-    if (rs.nred > 0) {
-      float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
-      for (int q = tid; q < rs.nslots; q += T) out[q] = make_float2(__int_as_float(0x7fc00000), 0.f);
-    }
+    cta_partials_nan(rs);
     return;
   }
   if (rs.nred == 0) return;
-
-  // ---- CTA reduction into the partial record (fixed order), reusing the staging buffers
-  float2* red = reinterpret_cast<float2*>(tsm);  // [warp][compact per-row slots]
-  const int nw = T >> 5;
-  float2* gred = red + nw * L.ncompact;          // [gram][row group][s x s]
-#pragma unroll
-  for (int ri = 0; ri < kMaxRed; ++ri) {
-    if (ri < rs.nred && rs.r[ri].kind != RED_GRAM) {
-      const RedSpec& r = rs.r[ri];
-      const int k = L.red_k[ri];
-      float2* dst = red + warp * L.ncompact + L.red_c[ri];
-      float2 v0 = acc.v[0][0], v1 = acc.v[0][1];
-      if (k == 1) { v0 = acc.v[1][0]; v1 = acc.v[1][1]; }
-      if (r.kind == RED_CDOT || r.kind == RED_GRAMV) {
-#pragma unroll
-        for (int off = 16; off >= GP; off >>= 1) {
-          v0 = cadd<float>(v0, shfl_down<float>(v0, off));
-          v1 = cadd<float>(v1, shfl_down<float>(v1, off));
-        }
-        if (lane < GP) { dst[2 * lane] = v0; dst[2 * lane + 1] = v1; }
-      } else {
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) v0 = cadd<float>(v0, shfl_down<float>(v0, off));
-        if (lane == 0) dst[0] = v0;
-      }
-    }
-  }
-  if (NG > 0 && grow < RG) {
-    gram_stage_block<S>(gred + (size_t)grow * S * S, ga0, gc0, g0[0], g0[1], g0[2], g0[3]);
-    if (NG > 1) gram_stage_block<S>(gred + ((size_t)RG + grow) * S * S, ga0, gc0, g1[0], g1[1], g1[2], g1[3]);
-  }
-  __syncthreads();
-  float2* out = reinterpret_cast<float2*>(rs.partials) + (size_t)blockIdx.x * rs.nslots;
-  for (int ri = 0; ri < rs.nred; ++ri) {  // per-row reductions: sum over warps in order
-    const RedSpec& r = rs.r[ri];
-    if (r.kind == RED_GRAM) continue;
-    const int cnt = (r.kind == RED_CDOT || r.kind == RED_GRAMV) ? S : 1;
-    for (int q = tid; q < cnt; q += T) {
-      float2 sum = make_float2(0.f, 0.f);
-      for (int w = 0; w < nw; ++w) sum = cadd<float>(sum, red[w * L.ncompact + L.red_c[ri] + q]);
-      out[r.slot + q] = sum;
-    }
-  }
-  for (int gi = 0; gi < NG; ++gi) {  // Grams: sum over row groups in order
-    for (int q = tid; q < S * S; q += T) {
-      float2 sum = make_float2(0.f, 0.f);
-      for (int g = 0; g < RG; ++g) sum = cadd<float>(sum, gred[((size_t)gi * RG + g) * S * S + q]);
-      out[L.gram_slot[gi] + q] = sum;
-    }
-  }
+  cta_partials<GP, NG>(tsm, rs, L, acc, g0, g1, grow, RG, ga0, gc0);
 }
 
 }  // namespace kr
