@@ -687,6 +687,30 @@ def bench_extras(kr, A, n, s, B, rp, ci, v, args, hbm_peak):
     out["mixed"] = {"method": "egl_bicg", **res,
                     "speedup": res["fp64"]["time_to_tol_ms"] / res["fp32_refine"]["time_to_tol_ms"],
                     "rel_diff_vs_fp64_gpu": diff}
+    # the same problem as a matrix-free stencil operator (complex64 products on the plane kernel,
+    # FP64 products from the stencil's coefficients): the same solves, timed the same way
+    from workloads import ConvDiff
+    cd = ConvDiff((args.grid,) * 3, (0.8, 0.8, 0.8), 0.05j)
+    St = kr.Operator.stencil(cd.dims, *cd.coefficients())
+    try:
+        sres = {}
+        for prec, name in ((kr.FP64, "fp64"), (kr.FP32_REFINE, "fp32_refine")):
+            X = torch.zeros_like(Bd)
+            kr.kr_solve(St, "egl_bicg", Bd, X, tol=args.tol, maxit=2000, precision=prec, check_every=1)
+            times = []
+            for _ in range(3):
+                X.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, inf = kr.kr_solve(St, "egl_bicg", Bd, X, tol=args.tol, maxit=2000, precision=prec, check_every=1)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            sres[name] = {"time_to_tol_ms": 1000 * statistics.median(times), "iters": inf.iters,
+                          "outer": inf.outer_iters, "relres_true": inf.relres_true, "status": inf.status}
+        out["mixed_stencil"] = {"method": "egl_bicg", "operator": "matrix-free 7-point stencil of the same A", **sres,
+                                "speedup": sres["fp64"]["time_to_tol_ms"] / sres["fp32_refine"]["time_to_tol_ms"]}
+    finally:
+        St.close()
     return out
 
 
