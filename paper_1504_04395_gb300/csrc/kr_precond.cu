@@ -8,7 +8,10 @@
 // schedule: a row's level is one more than the deepest level among the rows it depends on,
 // so all rows of one level can be solved at once.  A triangular solve of an n x s block is
 // one launch per level, G threads per row (one per column), rows of the level spread over
-// the grid; the launches of a level read only rows finished by earlier launches.
+// the grid; the launches of a level read only rows finished by earlier launches.  The level
+// launches are programmatic dependent launches: each is scheduled while the previous one is
+// still running and waits (griddepcontrol.wait) until that one has completed and its writes are
+// visible, so the launch latency between levels is hidden.
 #include <algorithm>
 #include <cmath>
 
@@ -108,6 +111,10 @@ __global__ void __launch_bounds__(kThreads) trsv_level_kernel(const int32_t* __r
                                                               const double2* __restrict__ invdiag, int s,
                                                               const double2* V, double2* Y) {
   constexpr int RPW = 32 / G;
+  // the previous level's launch has completed and its rows are visible; then this level's own
+  // dependent (the next level) may be scheduled
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane & (G - 1);
   const int64_t r = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * RPW + lane / G;
@@ -133,8 +140,18 @@ void trsv_go(const TriDev& t, int s, const double2* V, double2* Y, cudaStream_t 
     const int64_t b = t.h_lev_ptr[l], cnt = t.h_lev_ptr[l + 1] - b;
     if (cnt == 0) continue;
     const int64_t grid = (cnt + rows_per_cta - 1) / rows_per_cta;
-    trsv_level_kernel<G><<<(unsigned)grid, kThreads, 0, st>>>(t.lev_rows + b, cnt, t.rowptr, t.colidx, t.vals,
-                                                              t.invdiag, s, V, Y);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    KR_CUDA(cudaLaunchKernelEx(&cfg, trsv_level_kernel<G>, (const int32_t*)(t.lev_rows + b), cnt,
+                               (const int64_t*)t.rowptr, (const int32_t*)t.colidx, (const double2*)t.vals,
+                               (const double2*)t.invdiag, s, V, Y));
   }
   KR_CUDA(cudaGetLastError());
 }

@@ -165,7 +165,9 @@ __device__ __forceinline__ StencilCoef<T> stencil_coef(const SpmmArgs<T>& a) {
 
 // (A V)[j][c] for one thread of row j's group (G threads per row): the matrix-free stencil or
 // the CSR product, before any scaling.  act = row j exists and c < s; rowok = row j exists.
-template <typename T, int G>
+// GROUPED: the stencil's loads issued in two groups ahead of their FMAs (more registers); the
+// product kernel takes it, the fused linear-combination kernels keep one load at a time.
+template <typename T, int G, bool GROUPED>
 __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoef<T>& sk, int64_t j, int c,
                                           bool rowok, bool act) {
   const int s = a.s;
@@ -177,24 +179,56 @@ __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoe
     int64_t xc[3];
     grid_coords<3>(j, a.nst, a.sdiv32, a.sdims, a.sdiv, xc);
     if (act) {
-      y = cmul<T>(stc, a.V[j * s + c]);
+      if constexpr (GROUPED) {
+        // the loads of a group (centre and minus neighbours, then plus neighbours) are issued before
+        // its FMAs (an absent neighbour loads the centre again and is not used), so they are in
+        // flight together; two groups keep the registers of the complex128 kernels in bounds
+        bool has[6];
+        int64_t nb[6];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int qa = 2 - q;
-        if (qa < a.nst && xc[qa] > 0) {
-          const C2<T> xv = a.V[(j - a.sstr[qa]) * s + c];
-          const C2<T> m = sk.m[qa];
-          if (a.sreal) y = cfmareal<T>(m.x, xv, y);
-          else y = cfma<T>(m, xv, y);
+        for (int q = 0; q < 3; ++q) {
+          const int qa = 2 - q;
+          has[q] = qa < a.nst && xc[qa] > 0;
+          nb[q] = has[q] ? j - a.sstr[qa] : j;
+          has[3 + q] = q < a.nst && xc[q] < a.sdims[q] - 1;
+          nb[3 + q] = has[3 + q] ? j + a.sstr[q] : j;
         }
-      }
+        const C2<T> xv = a.V[j * s + c];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q < a.nst && xc[q] < a.sdims[q] - 1) {
-          const C2<T> xv = a.V[(j + a.sstr[q]) * s + c];
-          const C2<T> pp = sk.p[q];
-          if (a.sreal) y = cfmareal<T>(pp.x, xv, y);
-          else y = cfma<T>(pp, xv, y);
+        for (int g = 0; g < 2; ++g) {
+          C2<T> x[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) x[m] = a.V[nb[3 * g + m] * s + c];
+          if (g == 0) y = cmul<T>(stc, xv);
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            if (has[3 * g + m]) {
+              const C2<T> k = g == 0 ? sk.m[2 - m] : sk.p[m];
+              if (a.sreal) y = cfmareal<T>(k.x, x[m], y);
+              else y = cfma<T>(k, x[m], y);
+            }
+          }
+        }
+      } else {
+        y = cmul<T>(stc, a.V[j * s + c]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int qa = 2 - q;
+          if (qa < a.nst && xc[qa] > 0) {
+            const C2<T> xv = a.V[(j - a.sstr[qa]) * s + c];
+            const C2<T> m = sk.m[qa];
+            if (a.sreal) y = cfmareal<T>(m.x, xv, y);
+            else y = cfma<T>(m, xv, y);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q < a.nst && xc[q] < a.sdims[q] - 1) {
+            const C2<T> xv = a.V[(j + a.sstr[q]) * s + c];
+            const C2<T> pp = sk.p[q];
+            if (a.sreal) y = cfmareal<T>(pp.x, xv, y);
+            else y = cfma<T>(pp, xv, y);
+          }
         }
       }
     }
@@ -270,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
-    C2<T> y = spmm_row<T, G>(a, sk, j, c, rowok, act);
+    C2<T> y = spmm_row<T, G, true>(a, sk, j, c, rowok, act);
     if (act) {
       if (scaled) y = cmul<T>(ysc, y);
       if (a.Z != nullptr) {
@@ -346,7 +380,7 @@ __device__ __forceinline__ void lincomb_rows(const LinArgs& a, const RedSet& rs,
     const bool act = rowok && c < s;
     // the product's row, formed once (SRC_SPMM terms read it)
     C2<T> yprod = czero<T>();
-    if constexpr (SP) yprod = spmm_row<T, G>(sp, sk, j, c, rowok, act);
+    if constexpr (SP) yprod = spmm_row<T, G, false>(sp, sk, j, c, rowok, act);
     C2<T> o[kMaxOut];
 #pragma unroll
     for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();

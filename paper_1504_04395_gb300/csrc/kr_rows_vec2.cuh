@@ -158,8 +158,9 @@ __device__ __forceinline__ void cta_reduce2(const RedSet& rs, Acc2<NR>& acc, int
 }
 
 // (A V)[j] for the column pair p of row j (e = j * s + 2p, the pair's first element), before any
-// scaling: the matrix-free stencil (STENCIL) or the CSR product.  TAILBATCH: the last 1-3 entries
-// of a row as one predicated batch (needs registers; without it one entry at a time).
+// scaling: the matrix-free stencil (STENCIL) or the CSR product.  TAILBATCH: spend registers on
+// loads in flight -- CSR: the last 1-3 entries of a row as one predicated batch (without it one
+// entry at a time); stencil: every neighbour's load before the FMAs (without it one at a time).
 template <bool STENCIL, bool TAILBATCH>
 __device__ __forceinline__ Pair spmm2_row(const SpmmArgs<float>& a, const float2 stc, const float2 (&stm)[3],
                                           const float2 (&stp)[3], int64_t j, int p, int64_t e) {
@@ -169,24 +170,52 @@ __device__ __forceinline__ Pair spmm2_row(const SpmmArgs<float>& a, const float2
   if constexpr (STENCIL) {
     int64_t xc[3];
     grid_coords<3>(j, a.nst, a.sdiv32, a.sdims, a.sdiv, xc);
-    const Pair xv = ld_pair(a.V, e);
-    y.a = cmul<float>(stc, xv.a);
-    y.b = cmul<float>(stc, xv.b);
+    if constexpr (TAILBATCH) {
+      // all seven loads before the FMAs (an absent neighbour loads the centre again, unused)
+      bool has[6];
+      int64_t off[6];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int qa = 2 - q;
-      if (qa < a.nst && xc[qa] > 0) {
-        const Pair x = ld_pair(a.V, e - a.sstr[qa] * s);
-        if (a.sreal) { y.a = cfmareal<float>(stm[qa].x, x.a, y.a); y.b = cfmareal<float>(stm[qa].x, x.b, y.b); }
-        else { y.a = cfma<float>(stm[qa], x.a, y.a); y.b = cfma<float>(stm[qa], x.b, y.b); }
+      for (int q = 0; q < 3; ++q) {
+        const int qa = 2 - q;
+        has[q] = qa < a.nst && xc[qa] > 0;
+        off[q] = has[q] ? -a.sstr[qa] * s : 0;
+        has[3 + q] = q < a.nst && xc[q] < a.sdims[q] - 1;
+        off[3 + q] = has[3 + q] ? a.sstr[q] * s : 0;
       }
-    }
+      const Pair xv = ld_pair(a.V, e);
+      Pair x[6];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (q < a.nst && xc[q] < a.sdims[q] - 1) {
-        const Pair x = ld_pair(a.V, e + a.sstr[q] * s);
-        if (a.sreal) { y.a = cfmareal<float>(stp[q].x, x.a, y.a); y.b = cfmareal<float>(stp[q].x, x.b, y.b); }
-        else { y.a = cfma<float>(stp[q], x.a, y.a); y.b = cfma<float>(stp[q], x.b, y.b); }
+      for (int m = 0; m < 6; ++m) x[m] = ld_pair(a.V, e + off[m]);
+      y.a = cmul<float>(stc, xv.a);
+      y.b = cmul<float>(stc, xv.b);
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        if (has[m]) {
+          const float2 k = m < 3 ? stm[2 - m] : stp[m - 3];
+          if (a.sreal) { y.a = cfmareal<float>(k.x, x[m].a, y.a); y.b = cfmareal<float>(k.x, x[m].b, y.b); }
+          else { y.a = cfma<float>(k, x[m].a, y.a); y.b = cfma<float>(k, x[m].b, y.b); }
+        }
+      }
+    } else {
+      const Pair xv = ld_pair(a.V, e);
+      y.a = cmul<float>(stc, xv.a);
+      y.b = cmul<float>(stc, xv.b);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int qa = 2 - q;
+        if (qa < a.nst && xc[qa] > 0) {
+          const Pair x = ld_pair(a.V, e - a.sstr[qa] * s);
+          if (a.sreal) { y.a = cfmareal<float>(stm[qa].x, x.a, y.a); y.b = cfmareal<float>(stm[qa].x, x.b, y.b); }
+          else { y.a = cfma<float>(stm[qa], x.a, y.a); y.b = cfma<float>(stm[qa], x.b, y.b); }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q < a.nst && xc[q] < a.sdims[q] - 1) {
+          const Pair x = ld_pair(a.V, e + a.sstr[q] * s);
+          if (a.sreal) { y.a = cfmareal<float>(stp[q].x, x.a, y.a); y.b = cfmareal<float>(stp[q].x, x.b, y.b); }
+          else { y.a = cfma<float>(stp[q], x.a, y.a); y.b = cfma<float>(stp[q], x.b, y.b); }
+        }
       }
     }
   } else {

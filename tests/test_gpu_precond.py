@@ -64,6 +64,25 @@ def test_apply_preconditioner_matches_oracle(kr, which, s):
     op.close()
 
 
+@pytest.mark.parametrize("dims", [(30, 28, 26), (70, 66)])
+@pytest.mark.parametrize("s", [1, 8])
+def test_apply_preconditioner_many_levels(kr, dims, s):
+    """Grids with 82 and 135 levels per triangular solve and hundreds of rows per level (several
+    CTAs per level, each level's launch overlapping the previous one's completion) against the
+    oracle, and twice in a row bitwise."""
+    n, rp, ci, v = conv(dims)
+    A = oracle.csr_matrix_from_arrays(n, rp, ci, v)
+    L, U = precond.ilu0(A)
+    op = kr.Operator(n, rp, ci, v).set_preconditioner("ilu0")
+    V = gaussian_block(n, s, seed=s + 2)
+    Y = kr.kr_op_apply_precond(op, dev(V))
+    assert rel(Y.cpu().numpy(), precond.apply_inverse(L, U, V)) < 1e-12
+    assert torch.equal(Y, kr.kr_op_apply_precond(op, dev(V)))
+    Yh = kr.kr_op_apply_precond(op, dev(V), adjoint=True).cpu().numpy()
+    assert rel(Yh, precond.apply_inverse_adjoint(L, U, V)) < 1e-12
+    op.close()
+
+
 GLOBAL = ["egl_bicg", "gl_bicg", "li_bicg", "gl_bicgstab", "gl_qmr", "egl_qmr", "li_qmr"]
 BLOCK = ["bl_bicg", "bl_bicg_rq", "bl_bicgstab", "bl_bicgstab_rq"]
 
@@ -140,3 +159,4 @@ def test_ilu0_on_3d_convection_diffusion(kr):
         res[prec] = info.iters
     assert res["ilu0"] < 0.7 * res[None], res
     op.close()
+
