@@ -165,14 +165,18 @@ __device__ __forceinline__ StencilCoef<T> stencil_coef(const SpmmArgs<T>& a) {
 
 // (A V)[j][c] for one thread of row j's group (G threads per row): the matrix-free stencil or
 // the CSR product, before any scaling.  act = row j exists and c < s; rowok = row j exists.
-// GROUPED: the stencil's loads issued in two groups ahead of their FMAs (more registers); the
-// product kernel takes it, the fused linear-combination kernels keep one load at a time.
-template <typename T, int G, bool GROUPED>
+// SM: 0 = the operator decides at run time (the fused linear-combination kernels: one stencil
+// load at a time); 1 = CSR only; 2 = stencil only, its loads issued in two groups ahead of their
+// FMAs (the product kernel has one instantiation for each storage, so the CSR one keeps its
+// registers).
+template <typename T, int G, int SM>
 __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoef<T>& sk, int64_t j, int c,
                                           bool rowok, bool act) {
+  constexpr bool GROUPED = SM == 2;
   const int s = a.s;
   C2<T> y = czero<T>();
-  if (rowok && a.nst > 0) {
+  const bool sten = SM == 2 || (SM == 0 && a.nst > 0);
+  if (rowok && sten) {
     // matrix-free stencil, same summation order as the real-off-diagonal CSR storage:
     // centre, then -axis d-1 .. -axis 0, then +axis 0 .. +axis d-1
     const C2<T> stc = sk.c;
@@ -232,7 +236,7 @@ __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoe
         }
       }
     }
-  } else if (rowok) {
+  } else if (rowok && SM != 2) {
     const int64_t k0 = a.rowptr[j], k1 = a.rowptr[j + 1];
     // batches of kBatch entries: all index, value and gathered-row loads of a batch are
     // issued before its FMAs, so several neighbour rows are in flight per thread
@@ -279,7 +283,8 @@ __device__ __forceinline__ C2<T> spmm_row(const SpmmArgs<T>& a, const StencilCoe
   return y;
 }
 
-template <typename T, int G, int NG>
+// STEN: the matrix-free stencil (else CSR storage)
+template <typename T, int G, int NG, bool STEN>
 __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs, const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(SpmmArgs<T> a, RedSet rs
     const int64_t j = base + warp * RPW + lane / G;
     const bool rowok = j < n;
     const bool act = rowok && c < s;
-    C2<T> y = spmm_row<T, G, true>(a, sk, j, c, rowok, act);
+    C2<T> y = spmm_row<T, G, STEN ? 2 : 1>(a, sk, j, c, rowok, act);
     if (act) {
       if (scaled) y = cmul<T>(ysc, y);
       if (a.Z != nullptr) {
@@ -380,7 +385,7 @@ __device__ __forceinline__ void lincomb_rows(const LinArgs& a, const RedSet& rs,
     const bool act = rowok && c < s;
     // the product's row, formed once (SRC_SPMM terms read it)
     C2<T> yprod = czero<T>();
-    if constexpr (SP) yprod = spmm_row<T, G, false>(sp, sk, j, c, rowok, act);
+    if constexpr (SP) yprod = spmm_row<T, G, 0>(sp, sk, j, c, rowok, act);
     C2<T> o[kMaxOut];
 #pragma unroll
     for (int oi = 0; oi < kMaxOut; ++oi) o[oi] = czero<T>();

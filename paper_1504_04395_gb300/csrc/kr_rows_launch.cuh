@@ -51,28 +51,35 @@ static int resident_grid(K kernel, size_t smem, int grid, std::unordered_map<siz
   return grid < cap ? grid : cap;
 }
 
-template <typename T, int G, int NG>
+template <typename T, int G, int NG, bool STEN>
 static void spmm_go(const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
   static std::atomic<uint64_t> attr{0};
-  allow_smem(spmm_kernel<T, G, NG>, attr);
+  allow_smem(spmm_kernel<T, G, NG, STEN>, attr);
   const size_t smem = rs.nred > 0 ? (size_t)(kThreads / 32) * rs.nslots * sizeof(C2<T>) : 0;
   if (smem > (size_t)kMaxDynSmem) throw CudaError{cudaErrorInvalidValue, "spmm: too many reduction slots"};
   thread_local std::unordered_map<size_t, int> occ;
-  grid = resident_grid(spmm_kernel<T, G, NG>, smem, grid, occ);
-  spmm_kernel<T, G, NG><<<grid, kThreads, smem, st>>>(a, rs, done);
+  grid = resident_grid(spmm_kernel<T, G, NG, STEN>, smem, grid, occ);
+  spmm_kernel<T, G, NG, STEN><<<grid, kThreads, smem, st>>>(a, rs, done);
   KR_CUDA(cudaGetLastError());
 }
 
-template <typename T, int G>
+template <typename T, int G, bool STEN>
 static void spmm_ng(int ng, const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done, cudaStream_t st) {
-  if (ng == 0) return spmm_go<T, G, 0>(a, rs, grid, done, st);
+  if (ng == 0) return spmm_go<T, G, 0, STEN>(a, rs, grid, done, st);
   if constexpr (NGCap<1, G>::ok) {
-    if (ng == 1) return spmm_go<T, G, 1>(a, rs, grid, done, st);
+    if (ng == 1) return spmm_go<T, G, 1, STEN>(a, rs, grid, done, st);
   }
   if constexpr (NGCap<2, G>::ok) {
-    if (ng == 2) return spmm_go<T, G, 2>(a, rs, grid, done, st);
+    if (ng == 2) return spmm_go<T, G, 2, STEN>(a, rs, grid, done, st);
   }
   throw CudaError{cudaErrorInvalidValue, "spmm: fused Gram count exceeds the register budget"};
+}
+
+template <typename T, int G>
+static void spmm_storage(int ng, const SpmmArgs<T>& a, const RedSet& rs, int& grid, const int* done,
+                         cudaStream_t st) {
+  if (a.nst > 0) return spmm_ng<T, G, true>(ng, a, rs, grid, done, st);
+  return spmm_ng<T, G, false>(ng, a, rs, grid, done, st);
 }
 
 template <typename T>
@@ -80,12 +87,12 @@ static void spmm_dispatch(const SpmmArgs<T>& a, const RedSet& rs, int& grid, con
   const int G = threads_per_row(a.s);
   const int ng = count_grams(rs);
   switch (G) {
-    case 1: return spmm_ng<T, 1>(ng, a, rs, grid, done, st);
-    case 2: return spmm_ng<T, 2>(ng, a, rs, grid, done, st);
-    case 4: return spmm_ng<T, 4>(ng, a, rs, grid, done, st);
-    case 8: return spmm_ng<T, 8>(ng, a, rs, grid, done, st);
-    case 16: return spmm_ng<T, 16>(ng, a, rs, grid, done, st);
-    case 32: return spmm_ng<T, 32>(ng, a, rs, grid, done, st);
+    case 1: return spmm_storage<T, 1>(ng, a, rs, grid, done, st);
+    case 2: return spmm_storage<T, 2>(ng, a, rs, grid, done, st);
+    case 4: return spmm_storage<T, 4>(ng, a, rs, grid, done, st);
+    case 8: return spmm_storage<T, 8>(ng, a, rs, grid, done, st);
+    case 16: return spmm_storage<T, 16>(ng, a, rs, grid, done, st);
+    case 32: return spmm_storage<T, 32>(ng, a, rs, grid, done, st);
   }
   throw CudaError{cudaErrorInvalidValue, "spmm: s out of range"};
 }

@@ -80,8 +80,14 @@ def test_stencil_complex_coefficients(kr):
 def test_stencil_solve_equals_csr_solve(kr, method):
     op, st, csr, A = pair(kr, (16, 16, 16), (0.8, 0.8, 0.8), 0.05j)
     B = torch.from_numpy(gaussian_block(op.n, 4, seed=2)).cuda()
+    # matrix-free operators run the algorithms' own order (no fused-product schedule): the same
+    # order as the CSR storage's solve with the fused schedule switched off
     Xs, i1 = kr.kr_solve(st, method, B, tol=1e-8, maxit=400)
-    Xc, i2 = kr.kr_solve(csr, method, B, tol=1e-8, maxit=400)
+    kr.kr_set_fused_products(False)
+    try:
+        Xc, i2 = kr.kr_solve(csr, method, B, tol=1e-8, maxit=400)
+    finally:
+        kr.kr_set_fused_products(True)
     assert i1.iters == i2.iters and i1.history == i2.history
     assert torch.equal(Xs, Xc)
     ref = oracle.solve(method, A, B.cpu().numpy(), tol=1e-8, maxit=400)
