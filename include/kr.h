@@ -347,12 +347,16 @@ KR_API kr_status kr_profile_read(kr_profile* out, int32_t reset);
  * returns KR_OK. */
 KR_API kr_status kr_set_column_pairs(int32_t enable);
 
-/* Kernel choice for complex64 CSR products (the paper has no counterpart).  With enable != 0
- * (the default), complex64 products of a CSR operator with s in {2, 4, 8, 16, 32}, at most
- * 1024 stored entries per tile of rows (128, 64 or 32 rows for s <= 8, 16, 32), at most two
- * fused s x s Grams and two distinct block operands of the fused reductions run on a kernel
- * that stages each row tile's row pointers, diagonal, indices, values and reduction operands
- * in shared memory with bulk asynchronous copies and forms the fused Grams from shared memory;
+/* Kernel choice for staged complex64 products (the paper has no counterpart).  With enable != 0
+ * (the default):
+ *  - complex64 products of a CSR operator with s in {4, 8, 16, 32}, at most 1024 stored entries
+ *    per tile of rows (128, 64 or 32 rows for s <= 8, 16, 32), at most two fused s x s Grams and
+ *    two distinct block operands of the fused reductions run on a kernel that stages each row
+ *    tile's row pointers, diagonal, indices, values and reduction operands in shared memory with
+ *    bulk asynchronous copies and forms the fused Grams from shared memory;
+ *  - complex64 products of a matrix-free 2D or 3D stencil operator with s in {2, 4, 8, 16, 32}
+ *    and at most one distinct block operand run on a kernel that marches the grid's planes
+ *    through shared memory, one TMA tensor copy per halo'd plane of an x-y tile.
  * enable == 0 leaves them to the column-pair and one-column kernels (kr_set_column_pairs).
  * Products are bitwise the same on all of them; reductions agree to FP32 rounding.
  * Process-wide; always returns KR_OK. */
