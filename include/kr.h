@@ -363,11 +363,11 @@ KR_API kr_status kr_set_column_pairs(int32_t enable);
 KR_API kr_status kr_set_tile_kernels(int32_t enable);
 
 /* Schedule of Gl-BiCG (Algorithm 2) and eGl-BiCG (Algorithm 4); the paper has no counterpart.
- * With enable != 0 (the default), for operators with a stored matrix (CSR, lattice in CSR form),
- * alpha's denominator tr(Ph^H A P) is taken as tr((A^H Ph)^H P), a reduction of the direction
- * update of P once A^H Ph is formed, and the update X += alpha P, R -= alpha A P,
- * Rh -= conj(alpha) A^H Ph runs in one pass that forms A P row by row without storing it (with a
- * preconditioner A P is stored first).  Matrix-free operators run the algorithms' own order.
+ * With enable != 0 (the default), alpha's denominator tr(Ph^H A P) is taken as tr((A^H Ph)^H P),
+ * a reduction of the direction update of P once A^H Ph is formed, and the update X += alpha P,
+ * R -= alpha A P, Rh -= conj(alpha) A^H Ph runs in one pass, which for CSR operators without
+ * preconditioner forms A P row by row without storing it (for the matrix-free lattice and with a
+ * preconditioner A P is stored first).  The matrix-free stencil runs the algorithms' own order.
  * Per iteration that reads and writes 2M + 8 Bv instead of 2M + 11 Bv for eGl-BiCG and
  * 2M + 17 Bv instead of 2M + 19 Bv for Gl-BiCG (M: one read of A, Bv: one n x s block).  The
  * iterates are those of the algorithms in exact arithmetic; rounding differs.  enable == 0

@@ -1743,10 +1743,10 @@ SolveOut run_solve(Operator& op, int method, int s, const void* B, void* X, cons
     return check();
   };
   Ctx<T> c{E, B, X, in.shadow, in.shadow_mode, 0};
-  // the fused-product schedules for stored matrices: on the matrix-free stencil the fused pass
-  // forms the product with one neighbour load at a time (its registers leave no room for more),
-  // and the algorithms' own order, whose products run on the product kernels, is faster (128^3,
-  // s = 8, 50 FP64 eGl-BiCG iterations: 106 ms against 131 ms)
+  // the fused-product schedules except on the matrix-free stencil: there the fused pass forms the
+  // product with one neighbour load at a time (its registers leave no room for more), and the
+  // algorithms' own order, whose products run on the product kernels, is faster (128^3, s = 8,
+  // 50 FP64 eGl-BiCG iterations: 106 ms against 131 ms)
   const bool fused_schedule = fused_products_enabled() && op.stA.d == 0;
   switch (method) {
     case KRM_GL_BICG:

@@ -459,10 +459,10 @@ def test_fused_schedule_against_oracle_and_literal(kr, method):
 
 @pytest.mark.parametrize("kind", ["stencil", "lattice", "ilu0", "mixed"])
 def test_fused_schedule_other_operators(kr, kind):
-    """eGl-BiCG with fused products on by default, on the operators where the library does not run
-    the fused pass over a stored matrix: the matrix-free stencil (the algorithms' own order there),
-    the matrix-free lattice and the ILU(0)-preconditioned CSR operator (product stored first, then
-    combined), and in mixed precision (complex64 inner solves): against the oracle or dense LU."""
+    """eGl-BiCG with fused products on (the default) on the other operators: the matrix-free stencil
+    (which runs the algorithms' own order), the matrix-free lattice and the ILU(0)-preconditioned
+    CSR operator (fused schedule, product stored first, then combined), and in mixed precision
+    (complex64 inner solves): against the oracle or dense LU."""
     method = "egl_bicg"
     if kind == "lattice":
         from workloads import Lattice4D, lattice_csr
