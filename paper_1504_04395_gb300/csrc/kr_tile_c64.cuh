@@ -267,7 +267,7 @@ __device__ __forceinline__ void tile_fma(const unsigned char* valbuf, int k, int
 // MODE: TileMode; NG: fused Grams (0..2); at most kTileRowReds per-row reductions.  The Grams are
 // formed by the whole CTA after each tile from the shared-memory copies of Y and U.
 template <int GP, int MODE, int NG>
-__global__ void __launch_bounds__(kTileThreadsMax, 2) spmm_tile_kernel(SpmmArgs<float> a, RedSet rs, TileLayout L,
+__global__ void __launch_bounds__(kTileThreadsMax, 4) spmm_tile_kernel(SpmmArgs<float> a, RedSet rs, TileLayout L,
                                                                         const int* done) {
   if (done != nullptr && *(volatile const int*)done) return;
   using K = TileKernel<GP, MODE>;

@@ -9,7 +9,7 @@ constexpr int kTileEcap = 1024;        // stored entries per tile held in shared
 constexpr int kTileStagesA = 3;        // row pointers / diagonal / U blocks: tiles in flight
 constexpr int kTileStagesB = 2;        // indices / values: tiles in flight
 constexpr int kTileMaxU = 2;           // distinct block operands of the reductions
-constexpr int kTileThreadsMax = 512;
+constexpr int kTileThreadsMax = 256;
 constexpr int kTileRowReds = 2;        // per-row reductions (trace, column dots, norm, sums)
 
 // Shared-memory layout of one launch (byte offsets, all multiples of 16) and the reduction maps,
