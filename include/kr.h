@@ -350,7 +350,7 @@ KR_API kr_status kr_set_column_pairs(int32_t enable);
 /* Kernel choice for staged complex64 products (the paper has no counterpart).  With enable != 0
  * (the default):
  *  - complex64 products of a CSR operator with s in {4, 8, 16, 32}, at most 1024 stored entries
- *    per tile of rows (128, 64 or 32 rows for s <= 8, 16, 32), at most two fused s x s Grams and
+ *    per tile of rows (128, 64, 32 or 16 rows for s = 4, 8, 16, 32), at most two fused s x s Grams and
  *    two distinct block operands of the fused reductions run on a kernel that stages each row
  *    tile's row pointers, diagonal, indices, values and reduction operands in shared memory with
  *    bulk asynchronous copies and forms the fused Grams from shared memory;
