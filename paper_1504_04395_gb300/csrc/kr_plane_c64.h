@@ -25,6 +25,10 @@ struct PlaneGeom {
   int total;
 };
 
+// Whether the driver provides the tensor-map encoder the plane product needs (else the other
+// complex64 product kernels run its launches).
+bool plane_kernels_available();
+
 // Launch the plane product (geometry and reduction maps from plane_layout in kr_rows_launch.cuh);
 // returns the grid launched.
 int launch_spmm_plane(const SpmmArgs<float>& a, const RedSet& rs, const TileLayout& L, const PlaneGeom& P,

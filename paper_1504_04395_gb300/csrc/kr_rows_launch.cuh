@@ -349,7 +349,7 @@ int launch_spmm(const SpmmArgs<T>& a, const RedSet& rs, int grid, const int* don
   if constexpr (sizeof(T) == 4) {
     TileLayout L;
     PlaneGeom P;
-    if (!done_launch && tile_kernels_enabled() && plane_layout(a, rs, L, P)) {
+    if (!done_launch && tile_kernels_enabled() && plane_layout(a, rs, L, P) && plane_kernels_available()) {
       grid = launch_spmm_plane(a, rs, L, P, done, st);
       done_launch = true;
     }

@@ -78,18 +78,26 @@ int launch_spmm_tile(const SpmmArgs<float>& a, const RedSet& rs, const TileLayou
 }
 
 // ---- stencil planes
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (null if the driver
+// does not provide it)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder_or_null() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q{};
     const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) (void)cudaGetLastError();  // leave no sticky error behind for the next check
     return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p)
                                                                   : nullptr;
   }();
+  return fn;
+}
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder_or_null();
   if (!fn) throw CudaError{cudaErrorNotSupported, "plane product: cuTensorMapEncodeTiled unavailable"};
   return fn;
 }
+
+bool plane_kernels_available() { return tensor_map_encoder_or_null() != nullptr; }
 
 // 4D map of an n x s complex64 block on an nx x ny x nz grid as floats {2s, nx, ny, nz}, box
 // {2s, bx, by, 1}; points outside the grid read as zeros
